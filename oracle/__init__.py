@@ -112,6 +112,18 @@ def element_f32(Q, L, nx):
     return np.clip(k, 0, nx - 1).astype(np.int32)
 
 
+def element_key(Q, L, nx, dtype):
+    """Element index decided in the given precision from values of that
+    precision: floor(Q * dtype(nx / L)), clamped to [0, nx-1].  Where a kernel
+    takes this integer decision in FP32 or FP64, the oracle takes it the same
+    way, so keys can be compared bit for bit."""
+    q = np.asarray(Q).astype(dtype)
+    inv_h = dtype(np.float64(nx) / np.float64(L))
+    k = np.floor(q * inv_h)
+    k = np.where(np.isfinite(k), k, 0).astype(np.int64)
+    return np.clip(k, 0, nx - 1).astype(np.int32)
+
+
 def deposit(Q, p_star, psi_star, L, nx, elem=None):
     """b_j = sum_a psi*_a phi_j(Q_a) - p*_a phi_j'(Q_a)  (Eq. rhs-assembly)."""
     Q = _f64(Q); ps = _f64(p_star); psi = _f64(psi_star)

@@ -1,0 +1,1133 @@
+// Host side of the C ABI declared in include/swpic.h: context lifetime,
+// argument checking, launch shapes, the step sequence and its CUDA-graph
+// capture, read-out, checkpoints and the autotuner.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "swpic_internal.cuh"
+
+using namespace swpic;
+
+namespace {
+
+constexpr int64_t kSortChunk = 16384;
+// fixed-point charge: the bound on |b| maps to 2^58, leaving 2^4 of headroom
+// below the 2^62 conversion limit for decorations that grow after set-up
+constexpr int kFixedBits = 58;
+constexpr uint32_t PASS_NO_WRITE = 1u << 10;   // host-only marker (never sent to the device)
+
+struct Op {
+    int kind;          // 0 pass, 1 sort (into scratch), 2 event
+    double c1, c2, cd;
+    uint32_t flags;
+    bool from_scratch;
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int64_t kernels = 0;
+    int n_passes = 0;
+};
+
+}  // namespace
+
+struct swpic_ctx {
+    // configuration
+    std::vector<swpic_config> cfg;
+    int R = 0;
+    std::vector<int64_t> off;
+    int64_t N = 0;
+    int prec = 32;
+    bool dec = true;
+    int mode = 0, d2 = 0, resort = 0, tpb = 256, bpsm = 4, cap = 4096;
+    bool graphs = true;
+    int dev = 0, nsm = 148;
+    std::string gpu_name;
+    std::vector<int> nx, mesh_off;
+    int total_mesh = 0, max_nx = 0;
+    // device buffers owned by the context
+    RunDev *d_runs = nullptr;
+    std::vector<RunDev> h_runs;
+    unsigned long long *d_acc = nullptr, *d_done = nullptr;
+    void *d_table = nullptr;
+    double *d_b = nullptr, *d_bt = nullptr, *d_e = nullptr, *d_phi = nullptr;
+    double *d_diag_acc = nullptr, *d_field_diag = nullptr, *d_mass = nullptr, *d_mabs = nullptr;
+    long long *d_steps = nullptr;
+    double *d_ring = nullptr;
+    int32_t *d_ring_count = nullptr, *d_err = nullptr;
+    // sorting
+    std::vector<SortChunk> h_chunks;
+    SortChunk *d_chunks = nullptr;
+    int n_chunks = 0;
+    int32_t *d_cnt = nullptr;
+    int64_t *d_pos = nullptr, *d_scan_tmp = nullptr;
+    int64_t cnt_len = 0, scan_blocks = 0;
+    double *d_partials = nullptr;
+    double *h_mabs = nullptr;   // pinned
+    // bound state
+    void *st[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};   // Q, P, qs, ps, psi
+    void *sc[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    void *scratch = nullptr;
+    int64_t scratch_bytes = 0;
+    cudaStream_t stream = nullptr;
+    bool bound = false;
+    // host bookkeeping
+    bool prepared = false;
+    int64_t step = 0;
+    int64_t last_diag_step = -1;
+    std::string err;
+    std::map<std::string, GraphEntry> graph_cache;
+    bool timing = false;
+    std::vector<cudaEvent_t> events;
+    int n_timed = 0;
+    int64_t launches = 0;
+};
+
+namespace {
+
+swpic_status fail(swpic_ctx *ctx, swpic_status s, const std::string &msg) {
+    if (ctx) ctx->err = msg;
+    return s;
+}
+swpic_status fail_cuda(swpic_ctx *ctx, const char *what, cudaError_t e) {
+    return fail(ctx, SWPIC_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define CK(call)                                                    \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return fail_cuda(ctx, #call, e_);    \
+    } while (0)
+
+size_t elem_size(int prec) { return prec == SWPIC_F64 ? 8 : 4; }
+int vec_width(int prec) { return prec == SWPIC_F64 ? 2 : 4; }
+int64_t seg_bytes(int64_t n, int prec) { return (n * (int64_t)elem_size(prec) + 255) / 256 * 256; }
+
+// Gauss-Legendre nodes and weights on [-1, 1] from their closed forms (n <= 5).
+bool gauss_legendre_closed(int n, double *x, double *w) {
+    switch (n) {
+        case 1: x[0] = 0.0; w[0] = 2.0; return true;
+        case 2: x[0] = -1.0 / std::sqrt(3.0); x[1] = -x[0]; w[0] = w[1] = 1.0; return true;
+        case 3:
+            x[0] = -std::sqrt(0.6); x[1] = 0.0; x[2] = std::sqrt(0.6);
+            w[0] = w[2] = 5.0 / 9.0; w[1] = 8.0 / 9.0; return true;
+        case 4: {
+            const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+            const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(6.0 / 5.0));
+            const double wa = (18.0 + std::sqrt(30.0)) / 36.0, wb = (18.0 - std::sqrt(30.0)) / 36.0;
+            x[0] = -b; x[1] = -a; x[2] = a; x[3] = b;
+            w[0] = wb; w[1] = wa; w[2] = wa; w[3] = wb; return true;
+        }
+        case 5: {
+            const double a = std::sqrt(5.0 - 2.0 * std::sqrt(10.0 / 7.0)) / 3.0;
+            const double b = std::sqrt(5.0 + 2.0 * std::sqrt(10.0 / 7.0)) / 3.0;
+            const double wa = (322.0 + 13.0 * std::sqrt(70.0)) / 900.0;
+            const double wb = (322.0 - 13.0 * std::sqrt(70.0)) / 900.0;
+            x[0] = -b; x[1] = -a; x[2] = 0.0; x[3] = a; x[4] = b;
+            w[0] = wb; w[1] = wa; w[2] = 128.0 / 225.0; w[3] = wa; w[4] = wb; return true;
+        }
+        default: return false;
+    }
+}
+
+swpic_status validate_cfg(const swpic_config &c, std::string &why) {
+    if (!(c.L > 0.0) || !std::isfinite(c.L)) { why = "L must be finite and > 0"; return SWPIC_EINVAL; }
+    if (!(c.dt > 0.0) || !std::isfinite(c.dt)) { why = "dt must be finite and > 0"; return SWPIC_EINVAL; }
+    if (c.nx < 2 || c.nx > SWPIC_NX_MAX) { why = "nx must be in [2, SWPIC_NX_MAX]"; return SWPIC_EINVAL; }
+    if (c.precision != SWPIC_F32 && c.precision != SWPIC_F64) { why = "precision must be 32 or 64"; return SWPIC_EINVAL; }
+    if (c.decorated != 0 && c.decorated != 1) { why = "decorated must be 0 or 1"; return SWPIC_EINVAL; }
+    if (c.deposit_mode != 0 && c.deposit_mode != 1) { why = "bad deposit_mode"; return SWPIC_EINVAL; }
+    if (c.d2_mode != SWPIC_D2_LUMPED && c.d2_mode != SWPIC_D2_NODAL) { why = "bad d2_mode"; return SWPIC_EINVAL; }
+    if (c.resort_every < 0) { why = "resort_every must be >= 0"; return SWPIC_EINVAL; }
+    if (c.threads_per_block != 0 &&
+        (c.threads_per_block < 64 || c.threads_per_block > 512 || c.threads_per_block % 32)) {
+        why = "threads_per_block must be 0 or a multiple of 32 in [64, 512]"; return SWPIC_EINVAL;
+    }
+    if (c.blocks_per_sm < 0 || c.blocks_per_sm > 32) { why = "blocks_per_sm must be in [0, 32]"; return SWPIC_EINVAL; }
+    if (c.diag_capacity < 0) { why = "diag_capacity must be >= 0"; return SWPIC_EINVAL; }
+    return SWPIC_OK;
+}
+
+void free_all(swpic_ctx *ctx) {
+    for (auto &kv : ctx->graph_cache) if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    ctx->graph_cache.clear();
+    for (auto ev : ctx->events) cudaEventDestroy(ev);
+    ctx->events.clear();
+    void *ptrs[] = {ctx->d_runs, ctx->d_acc, ctx->d_done, ctx->d_table, ctx->d_b, ctx->d_bt, ctx->d_e,
+                    ctx->d_phi, ctx->d_diag_acc, ctx->d_field_diag, ctx->d_mass, ctx->d_mabs,
+                    ctx->d_steps, ctx->d_ring, ctx->d_ring_count, ctx->d_err, ctx->d_chunks,
+                    ctx->d_cnt, ctx->d_pos, ctx->d_scan_tmp, ctx->d_partials};
+    for (void *p : ptrs) if (p) cudaFree(p);
+    if (ctx->h_mabs) cudaFreeHost(ctx->h_mabs);
+}
+
+void clear_graphs(swpic_ctx *ctx) {
+    for (auto &kv : ctx->graph_cache) if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    ctx->graph_cache.clear();
+}
+
+PassArgs base_args(swpic_ctx *ctx) {
+    PassArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.Qi = ctx->st[0]; a.Pi = ctx->st[1]; a.qsi = ctx->st[2]; a.psi_i = ctx->st[3]; a.wi = ctx->st[4];
+    a.Qo = ctx->st[0]; a.Po = ctx->st[1]; a.qso = ctx->st[2]; a.pso = ctx->st[3]; a.wo = ctx->st[4];
+    a.n_total = ctx->N;
+    a.n_runs = ctx->R;
+    a.d2_mode = ctx->d2;
+    a.max_nx = ctx->max_nx;
+    a.runs = ctx->d_runs;
+    a.acc = ctx->d_acc;
+    a.table = ctx->d_table;
+    a.b = ctx->d_b; a.btilde = ctx->d_bt; a.efield = ctx->d_e;
+    a.run_done = ctx->d_done;
+    a.diag_acc = ctx->d_diag_acc;
+    a.field_diag = ctx->d_field_diag;
+    a.mass = ctx->d_mass;
+    a.steps = ctx->d_steps;
+    a.ring = ctx->d_ring;
+    a.ring_count = ctx->d_ring_count;
+    a.ring_cap = ctx->cap;
+    a.err = ctx->d_err;
+    return a;
+}
+
+void pass_shape(const swpic_ctx *ctx, int *grid, int64_t *chunk) {
+    const int vw = vec_width(ctx->prec);
+    const int64_t gmax = (int64_t)ctx->nsm * ctx->bpsm;
+    const int64_t min_per = (int64_t)ctx->tpb * vw * 2;
+    int64_t g = (ctx->N + min_per - 1) / min_per;
+    g = std::max<int64_t>(1, std::min(g, gmax));
+    int64_t ch = (ctx->N + g - 1) / g;
+    ch = (ch + vw - 1) / vw * vw;
+    if (ch < vw) ch = vw;
+    g = (ctx->N + ch - 1) / ch;
+    *grid = (int)std::max<int64_t>(1, g);
+    *chunk = ch;
+}
+
+// Enqueue one particle pass.  The no-write variant points the outputs at the
+// inputs, which is harmless: a pass with c1 = c2 = cd = 0 rewrites identical values.
+swpic_status enqueue_pass(swpic_ctx *ctx, double c1, double c2, double cd, uint32_t flags,
+                          bool from_scratch) {
+    PassArgs a = base_args(ctx);
+    if (from_scratch) {
+        a.Qi = ctx->sc[0]; a.Pi = ctx->sc[1]; a.qsi = ctx->sc[2]; a.psi_i = ctx->sc[3]; a.wi = ctx->sc[4];
+        flags |= PASS_WRITE_PSI;
+    }
+    a.c1 = c1; a.c2 = c2; a.cd = cd;
+    a.flags = flags & 0xffu;
+    int grid;
+    int64_t chunk;
+    pass_shape(ctx, &grid, &chunk);
+    a.chunk = chunk;
+    const size_t smem = pass_smem_bytes(ctx->prec, ctx->max_nx, ctx->mode);
+    if (ctx->N > 0) {
+        CK(launch_pass(ctx->prec, ctx->dec, ctx->mode, a, grid, ctx->tpb, smem, ctx->stream));
+        ctx->launches += 1;
+    }
+    // Runs without particles have no CTA to finish them: their field stays zero,
+    // and they get no step counts or diagnostic records.
+    return SWPIC_OK;
+}
+
+swpic_status enqueue_sort(swpic_ctx *ctx) {
+    if (ctx->n_chunks == 0) return SWPIC_OK;
+    CK(launch_sort_hist(ctx->prec, ctx->st[0], ctx->d_runs, ctx->d_chunks, ctx->n_chunks, ctx->d_cnt,
+                        ctx->max_nx, ctx->stream));
+    CK(launch_scan(ctx->d_cnt, ctx->d_pos, ctx->cnt_len, ctx->d_scan_tmp, ctx->scan_blocks, ctx->stream));
+    const void *src[5] = {ctx->st[0], ctx->st[1], ctx->st[2], ctx->st[3], ctx->st[4]};
+    void *dst[5] = {ctx->sc[0], ctx->sc[1], ctx->sc[2], ctx->sc[3], ctx->sc[4]};
+    CK(launch_sort_scatter(ctx->prec, ctx->dec, src, dst, ctx->d_runs, ctx->d_chunks, ctx->n_chunks,
+                           ctx->d_pos, ctx->max_nx, ctx->stream));
+    ctx->launches += 5;
+    return SWPIC_OK;
+}
+
+swpic_status check_bound(swpic_ctx *ctx) {
+    if (!ctx) return SWPIC_EINVAL;
+    if (!ctx->bound) return fail(ctx, SWPIC_ESTATE, "no state bound (call swpic_bind_state)");
+    return SWPIC_OK;
+}
+
+swpic_status upload_runs(swpic_ctx *ctx) {
+    CK(cudaMemcpyAsync(ctx->d_runs, ctx->h_runs.data(), sizeof(RunDev) * ctx->R,
+                       cudaMemcpyHostToDevice, ctx->stream));
+    return SWPIC_OK;
+}
+
+// mass, fixed-point scale, field of the current positions, record at the current step
+swpic_status prepare(swpic_ctx *ctx, bool keep_steps) {
+    swpic_status s = check_bound(ctx);
+    if (s != SWPIC_OK) return s;
+    CK(launch_mass(ctx->prec, ctx->st[4], ctx->st[3], ctx->d_chunks, ctx->n_chunks, ctx->d_partials,
+                   ctx->R, ctx->d_mass, ctx->d_mabs, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->h_mabs, ctx->d_mabs, sizeof(double) * 2 * ctx->R, cudaMemcpyDeviceToHost,
+                       ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->launches += 2;
+    for (int r = 0; r < ctx->R; ++r) {
+        // every partial sum of the deposit is bounded by sum |psi*| + 2 sum |p*| / h
+        const double m = ctx->h_mabs[2 * r] + 2.0 * ctx->h_mabs[2 * r + 1] * ctx->h_runs[r].inv_h;
+        if (!std::isfinite(m)) return fail(ctx, SWPIC_ENUMERIC, "non-finite particle weights");
+        int k = kFixedBits;
+        if (m > 0.0) k = kFixedBits - (int)std::ceil(std::log2(m));
+        k = std::max(-1000, std::min(1000, k));
+        ctx->h_runs[r].fx_scale = std::ldexp(1.0, k);
+        ctx->h_runs[r].fx_inv = std::ldexp(1.0, -k);
+    }
+    s = upload_runs(ctx);
+    if (s != SWPIC_OK) return s;
+    CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_done, 0, sizeof(unsigned long long) * ctx->R, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_diag_acc, 0, sizeof(double) * 2 * ctx->R, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_table, 0, (size_t)ctx->total_mesh * 2 * elem_size(ctx->prec), ctx->stream));
+    if (!keep_steps) {
+        CK(cudaMemsetAsync(ctx->d_steps, 0, sizeof(long long) * ctx->R, ctx->stream));
+        CK(cudaMemsetAsync(ctx->d_ring_count, 0, sizeof(int32_t) * ctx->R, ctx->stream));
+        ctx->step = 0;
+    }
+    s = enqueue_pass(ctx, 0.0, 0.0, 0.0, PASS_DEPOSIT | PASS_SOLVE | PASS_NO_WRITE, false);
+    if (s != SWPIC_OK) return s;
+    s = enqueue_pass(ctx, 0.0, 0.0, 0.0, PASS_DIAG | PASS_NO_WRITE, false);
+    if (s != SWPIC_OK) return s;
+    ctx->last_diag_step = ctx->step;
+    ctx->prepared = true;
+    clear_graphs(ctx);
+    return SWPIC_OK;
+}
+
+swpic_status ensure_prepared(swpic_ctx *ctx) {
+    swpic_status s = check_bound(ctx);
+    if (s != SWPIC_OK) return s;
+    if (!ctx->prepared) return prepare(ctx, false);
+    return SWPIC_OK;
+}
+
+swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets, swpic_ctx **out) {
+    if (!out) return SWPIC_EINVAL;
+    *out = nullptr;
+    if (!cfgs || R < 1 || !offsets) return SWPIC_EINVAL;
+    std::string why;
+    for (int r = 0; r < R; ++r) {
+        swpic_status s = validate_cfg(cfgs[r], why);
+        if (s != SWPIC_OK) return s;
+        const swpic_config &a = cfgs[0], &b = cfgs[r];
+        if (a.precision != b.precision || a.decorated != b.decorated || a.deposit_mode != b.deposit_mode ||
+            a.d2_mode != b.d2_mode)
+            return SWPIC_EINVAL;
+    }
+    if (offsets[0] != 0) return SWPIC_EINVAL;
+    for (int r = 0; r < R; ++r) if (offsets[r + 1] < offsets[r]) return SWPIC_EINVAL;
+    if (offsets[R] > ((int64_t)1 << 40)) return SWPIC_EINVAL;
+    swpic_ctx *ctx = new (std::nothrow) swpic_ctx();
+    if (!ctx) return SWPIC_ENOMEM;
+    ctx->cfg.assign(cfgs, cfgs + R);
+    ctx->R = R;
+    ctx->off.assign(offsets, offsets + R + 1);
+    ctx->N = offsets[R];
+    const swpic_config &c0 = cfgs[0];
+    ctx->prec = c0.precision;
+    ctx->dec = c0.decorated != 0;
+    ctx->mode = c0.deposit_mode;
+    ctx->d2 = c0.d2_mode;
+    ctx->resort = c0.resort_every;
+    ctx->tpb = c0.threads_per_block ? c0.threads_per_block : 256;
+    ctx->bpsm = c0.blocks_per_sm ? c0.blocks_per_sm : 4;
+    ctx->graphs = c0.use_graphs != 0;
+    ctx->cap = c0.diag_capacity ? c0.diag_capacity : 4096;
+    auto bail = [&](swpic_status s) { free_all(ctx); delete ctx; return s; };
+    if (cudaGetDevice(&ctx->dev) != cudaSuccess) return bail(SWPIC_ECUDA);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, ctx->dev) != cudaSuccess) return bail(SWPIC_ECUDA);
+    ctx->nsm = prop.multiProcessorCount;
+    ctx->gpu_name = prop.name;
+    ctx->nx.resize(R);
+    ctx->mesh_off.resize(R);
+    ctx->h_runs.resize(R);
+    int mo = 0;
+    for (int r = 0; r < R; ++r) {
+        const swpic_config &c = cfgs[r];
+        RunDev &d = ctx->h_runs[r];
+        std::memset(&d, 0, sizeof(d));
+        d.p0 = offsets[r];
+        d.p1 = offsets[r + 1];
+        d.L = c.L;
+        d.nx = c.nx;
+        d.h = c.L / c.nx;
+        d.inv_h = (double)c.nx / c.L;
+        d.inv_L = 1.0 / c.L;
+        d.dt = c.dt;
+        d.Lf = (float)c.L;
+        d.inv_hf = (float)d.inv_h;
+        d.inv_Lf = (float)d.inv_L;
+        d.dtf = (float)c.dt;
+        d.fx_scale = std::ldexp(1.0, 56);
+        d.fx_inv = std::ldexp(1.0, -56);
+        d.mesh_off = mo;
+        ctx->nx[r] = c.nx;
+        ctx->mesh_off[r] = mo;
+        mo += c.nx;
+        ctx->max_nx = std::max(ctx->max_nx, c.nx);
+    }
+    ctx->total_mesh = mo;
+    // sort chunks (also used by the mass reduction)
+    int64_t cnt_base = 0;
+    for (int r = 0; r < R; ++r) {
+        const int64_t n = offsets[r + 1] - offsets[r];
+        if (n == 0) continue;
+        const int nch = (int)((n + kSortChunk - 1) / kSortChunk);
+        for (int k = 0; k < nch; ++k) {
+            SortChunk sc;
+            sc.start = offsets[r] + (int64_t)k * kSortChunk;
+            sc.end = std::min(offsets[r + 1], sc.start + kSortChunk);
+            sc.cnt_base = cnt_base;
+            sc.run = r;
+            sc.local = k;
+            sc.nch = nch;
+            sc.pad = 0;
+            ctx->h_chunks.push_back(sc);
+        }
+        cnt_base += (int64_t)ctx->nx[r] * nch;
+    }
+    ctx->n_chunks = (int)ctx->h_chunks.size();
+    ctx->cnt_len = cnt_base;
+    ctx->scan_blocks = scan_block_count(std::max<int64_t>(1, cnt_base));
+    const size_t es = elem_size(ctx->prec);
+    auto alloc = [&](void **p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
+    bool ok = true;
+    ok &= alloc((void **)&ctx->d_runs, sizeof(RunDev) * R);
+    ok &= alloc((void **)&ctx->d_acc, sizeof(unsigned long long) * mo);
+    ok &= alloc((void **)&ctx->d_done, sizeof(unsigned long long) * R);
+    ok &= alloc(&ctx->d_table, (size_t)mo * 2 * es);
+    ok &= alloc((void **)&ctx->d_b, sizeof(double) * mo);
+    ok &= alloc((void **)&ctx->d_bt, sizeof(double) * mo);
+    ok &= alloc((void **)&ctx->d_e, sizeof(double) * mo);
+    ok &= alloc((void **)&ctx->d_phi, sizeof(double) * mo);
+    ok &= alloc((void **)&ctx->d_diag_acc, sizeof(double) * 2 * R);
+    ok &= alloc((void **)&ctx->d_field_diag, sizeof(double) * 2 * R);
+    ok &= alloc((void **)&ctx->d_mass, sizeof(double) * R);
+    ok &= alloc((void **)&ctx->d_mabs, sizeof(double) * 2 * R);
+    ok &= alloc((void **)&ctx->d_steps, sizeof(long long) * R);
+    ok &= alloc((void **)&ctx->d_ring, sizeof(double) * kDiagWords * (size_t)R * ctx->cap);
+    ok &= alloc((void **)&ctx->d_ring_count, sizeof(int32_t) * R);
+    ok &= alloc((void **)&ctx->d_err, sizeof(int32_t));
+    ok &= alloc((void **)&ctx->d_chunks, sizeof(SortChunk) * std::max(1, ctx->n_chunks));
+    ok &= alloc((void **)&ctx->d_cnt, sizeof(int32_t) * std::max<int64_t>(1, cnt_base));
+    ok &= alloc((void **)&ctx->d_pos, sizeof(int64_t) * std::max<int64_t>(1, cnt_base));
+    ok &= alloc((void **)&ctx->d_scan_tmp, sizeof(int64_t) * ctx->scan_blocks);
+    ok &= alloc((void **)&ctx->d_partials, sizeof(double) * 3 * std::max(1, ctx->n_chunks));
+    ok &= cudaMallocHost((void **)&ctx->h_mabs, sizeof(double) * 2 * R) == cudaSuccess;
+    if (!ok) return bail(SWPIC_ENOMEM);
+    if (cudaMemcpy(ctx->d_runs, ctx->h_runs.data(), sizeof(RunDev) * R, cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(SWPIC_ECUDA);
+    if (ctx->n_chunks &&
+        cudaMemcpy(ctx->d_chunks, ctx->h_chunks.data(), sizeof(SortChunk) * ctx->n_chunks,
+                   cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(SWPIC_ECUDA);
+    cudaMemset(ctx->d_err, 0, sizeof(int32_t));
+    cudaMemset(ctx->d_acc, 0, sizeof(unsigned long long) * mo);
+    cudaMemset(ctx->d_done, 0, sizeof(unsigned long long) * R);
+    cudaMemset(ctx->d_steps, 0, sizeof(long long) * R);
+    cudaMemset(ctx->d_ring_count, 0, sizeof(int32_t) * R);
+    cudaMemset(ctx->d_diag_acc, 0, sizeof(double) * 2 * R);
+    cudaMemset(ctx->d_field_diag, 0, sizeof(double) * 2 * R);
+    cudaMemset(ctx->d_table, 0, (size_t)mo * 2 * es);
+    if (cudaDeviceSynchronize() != cudaSuccess) return bail(SWPIC_ECUDA);
+    *out = ctx;
+    return SWPIC_OK;
+}
+
+// Build the op list of n steps starting at ctx->step.
+std::vector<Op> build_ops(swpic_ctx *ctx, int n, int d) {
+    std::vector<Op> ops;
+    const int64_t s0 = ctx->step;
+    const bool can_sort = ctx->resort > 0 && ctx->scratch != nullptr && ctx->n_chunks > 0;
+    for (int i = 0; i <= n; ++i) {
+        const int64_t s = s0 + i;
+        bool sorted = false;
+        if (i < n && can_sort && s % ctx->resort == 0 && s > 0) {
+            ops.push_back(Op{1, 0, 0, 0, 0, false});
+            sorted = true;
+        }
+        Op p{0, 0, 0, 0, 0, sorted};
+        bool diag = d > 0 && s % d == 0;
+        if (i == 0) {
+            diag = diag && ctx->last_diag_step != s;
+            p.c1 = 0.0; p.c2 = 0.5; p.cd = 1.0;
+            p.flags = PASS_DEPOSIT | PASS_SOLVE | PASS_COUNT_STEP;
+        } else if (i < n) {
+            p.c1 = 0.5; p.c2 = 0.5; p.cd = 1.0;
+            p.flags = PASS_DEPOSIT | PASS_SOLVE | PASS_COUNT_STEP;
+        } else {
+            p.c1 = 0.5; p.c2 = 0.0; p.cd = 0.0;
+            p.flags = 0;
+        }
+        if (diag) p.flags |= PASS_DIAG;
+        ops.push_back(p);
+    }
+    return ops;
+}
+
+std::string ops_key(const swpic_ctx *ctx, const std::vector<Op> &ops) {
+    std::string k = std::to_string(ctx->tpb) + "/" + std::to_string(ctx->bpsm) + "/" +
+                    std::to_string(ctx->timing ? 1 : 0) + ":";
+    for (const Op &o : ops) {
+        k += o.kind == 1 ? 'S' : 'P';
+        if (o.kind == 0) {
+            char buf[48];
+            std::snprintf(buf, sizeof(buf), "%.2g,%.2g,%.2g,%x,%d;", o.c1, o.c2, o.cd, o.flags,
+                          o.from_scratch ? 1 : 0);
+            k += buf;
+        }
+    }
+    return k;
+}
+
+swpic_status ensure_events(swpic_ctx *ctx, size_t n) {
+    while (ctx->events.size() < n) {
+        cudaEvent_t e;
+        CK(cudaEventCreate(&e));
+        ctx->events.push_back(e);
+    }
+    return SWPIC_OK;
+}
+
+swpic_status enqueue_ops(swpic_ctx *ctx, const std::vector<Op> &ops, int64_t *kernels, int *passes) {
+    const int64_t l0 = ctx->launches;
+    int np = 0;
+    int npass = 0;
+    for (const Op &o : ops) if (o.kind == 0) ++npass;
+    if (ctx->timing) {
+        swpic_status s = ensure_events(ctx, 2 * (size_t)npass);
+        if (s != SWPIC_OK) return s;
+    }
+    for (const Op &o : ops) {
+        swpic_status s;
+        if (o.kind == 1) {
+            s = enqueue_sort(ctx);
+        } else {
+            if (ctx->timing) CK(cudaEventRecord(ctx->events[2 * np], ctx->stream));
+            s = enqueue_pass(ctx, o.c1, o.c2, o.cd, o.flags, o.from_scratch);
+            if (ctx->timing) CK(cudaEventRecord(ctx->events[2 * np + 1], ctx->stream));
+            ++np;
+        }
+        if (s != SWPIC_OK) return s;
+    }
+    if (kernels) *kernels = ctx->launches - l0;
+    if (passes) *passes = np;
+    return SWPIC_OK;
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+int32_t swpic_abi_version(void) { return SWPIC_ABI_VERSION; }
+
+const char *swpic_status_string(swpic_status s) {
+    switch (s) {
+        case SWPIC_OK: return "ok";
+        case SWPIC_EINVAL: return "invalid argument";
+        case SWPIC_ENOMEM: return "out of memory";
+        case SWPIC_ECUDA: return "CUDA error";
+        case SWPIC_ETIMEOUT: return "device wait timed out";
+        case SWPIC_ENUMERIC: return "numeric anomaly (accumulator overflow or non-finite field)";
+        case SWPIC_EUNSUPPORTED: return "unsupported";
+        case SWPIC_ESTATE: return "call out of order";
+        case SWPIC_EIO: return "I/O error";
+    }
+    return "unknown status";
+}
+
+const char *swpic_last_error(const swpic_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+swpic_status swpic_create(const swpic_config *cfg, int64_t n_particles, swpic_ctx **out) {
+    if (n_particles < 0) return SWPIC_EINVAL;
+    int64_t off[2] = {0, n_particles};
+    return create_impl(cfg, 1, off, out);
+}
+
+swpic_status swpic_create_batch(const swpic_config *cfgs, int32_t n_runs,
+                                const int64_t *particle_offsets, swpic_ctx **out) {
+    return create_impl(cfgs, n_runs, particle_offsets, out);
+}
+
+void swpic_destroy(swpic_ctx *ctx) {
+    if (!ctx) return;
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    else cudaDeviceSynchronize();
+    free_all(ctx);
+    delete ctx;
+}
+
+swpic_status swpic_scratch_bytes(const swpic_ctx *ctx, int64_t *bytes) {
+    if (!ctx || !bytes) return SWPIC_EINVAL;
+    *bytes = (ctx->dec ? 5 : 3) * seg_bytes(ctx->N, ctx->prec);
+    return SWPIC_OK;
+}
+
+swpic_status swpic_bind_state(swpic_ctx *ctx, void *Q, void *P, void *qs, void *ps, void *psi,
+                              void *scratch, int64_t scratch_bytes, swpic_stream stream) {
+    if (!ctx) return SWPIC_EINVAL;
+    if (ctx->N > 0) {
+        if (!Q || !P || !psi) return fail(ctx, SWPIC_EINVAL, "Q, P and psi are required");
+        if (ctx->dec && (!qs || !ps)) return fail(ctx, SWPIC_EINVAL, "decorated runs need qs and ps");
+        void *all[5] = {Q, P, qs, ps, psi};
+        for (void *p : all)
+            if (p && (reinterpret_cast<uintptr_t>(p) & 15))
+                return fail(ctx, SWPIC_EINVAL, "state arrays must be 16-byte aligned");
+    }
+    int64_t need = 0;
+    swpic_scratch_bytes(ctx, &need);
+    if (scratch && scratch_bytes < need) return fail(ctx, SWPIC_EINVAL, "scratch too small");
+    if (scratch && (reinterpret_cast<uintptr_t>(scratch) & 255))
+        return fail(ctx, SWPIC_EINVAL, "scratch must be 256-byte aligned");
+    ctx->st[0] = Q; ctx->st[1] = P; ctx->st[2] = ctx->dec ? qs : nullptr;
+    ctx->st[3] = ctx->dec ? ps : nullptr; ctx->st[4] = psi;
+    ctx->scratch = scratch;
+    ctx->scratch_bytes = scratch_bytes;
+    for (int k = 0; k < 5; ++k) ctx->sc[k] = nullptr;
+    if (scratch) {
+        const int64_t seg = seg_bytes(ctx->N, ctx->prec);
+        char *b = reinterpret_cast<char *>(scratch);
+        if (ctx->dec) {
+            for (int k = 0; k < 5; ++k) ctx->sc[k] = b + k * seg;
+        } else {
+            ctx->sc[0] = b; ctx->sc[1] = b + seg; ctx->sc[4] = b + 2 * seg;
+        }
+    }
+    ctx->stream = reinterpret_cast<cudaStream_t>(stream);
+    ctx->bound = true;
+    ctx->prepared = false;
+    clear_graphs(ctx);
+    return SWPIC_OK;
+}
+
+swpic_status swpic_init_particles(swpic_ctx *ctx, const double *Q, const double *P, const double *qs,
+                                  const double *ps, const double *psi, int64_t n) {
+    swpic_status s = check_bound(ctx);
+    if (s != SWPIC_OK) return s;
+    if (n != ctx->N) return fail(ctx, SWPIC_EINVAL, "n must equal the total particle count");
+    if (n > 0 && (!Q || !P || !psi)) return fail(ctx, SWPIC_EINVAL, "Q, P and psi are required");
+    if (n > 0) {
+        double *stage = nullptr;
+        CK(cudaMallocAsync((void **)&stage, sizeof(double) * n, ctx->stream));
+        const double *src[5] = {Q, P, qs, ps, psi};
+        for (int k = 0; k < 5; ++k) {
+            if (!ctx->st[k]) continue;
+            if (src[k]) {
+                CK(cudaMemcpyAsync(stage, src[k], sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+                CK(launch_convert(ctx->prec, stage, ctx->st[k], n, ctx->stream));
+                ctx->launches += 1;
+            } else {
+                CK(cudaMemsetAsync(ctx->st[k], 0, (size_t)n * elem_size(ctx->prec), ctx->stream));
+            }
+        }
+        CK(cudaFreeAsync(stage, ctx->stream));
+    }
+    return prepare(ctx, false);
+}
+
+swpic_status swpic_init_lattice(swpic_ctx *ctx, int32_t run, const swpic_lattice *spec,
+                                const double *jitter_x, const double *jitter_v) {
+    swpic_status s = check_bound(ctx);
+    if (s != SWPIC_OK) return s;
+    if (!spec || run < 0 || run >= ctx->R) return fail(ctx, SWPIC_EINVAL, "bad run or spec");
+    const int64_t n = (int64_t)spec->nq * spec->nv;
+    if (spec->nq < 1 || spec->nv < 1 || n != ctx->off[run + 1] - ctx->off[run])
+        return fail(ctx, SWPIC_EINVAL, "nq * nv must equal the run's particle count");
+    if (spec->n_terms < 1 || spec->n_terms > 4) return fail(ctx, SWPIC_EINVAL, "n_terms must be 1..4");
+    if (!(spec->vmax > spec->vmin)) return fail(ctx, SWPIC_EINVAL, "vmax must exceed vmin");
+    LatticeDev lat;
+    std::memset(&lat, 0, sizeof(lat));
+    lat.nq = spec->nq; lat.nv = spec->nv; lat.n_terms = spec->n_terms;
+    lat.quad_order = spec->quad_order; lat.decorate = spec->decorate && ctx->dec;
+    lat.vmin = spec->vmin; lat.vmax = spec->vmax; lat.alpha = spec->alpha; lat.kx = spec->kx;
+    for (int m = 0; m < 4; ++m) {
+        lat.amp[m] = spec->amp[m]; lat.c0[m] = spec->c0[m]; lat.c2[m] = spec->c2[m];
+        lat.beta[m] = spec->beta[m]; lat.u[m] = spec->u[m];
+    }
+    if (!gauss_legendre_closed(lat.quad_order, lat.gx, lat.gw))
+        return fail(ctx, SWPIC_EINVAL, "quad_order must be 1..5");
+    double *dj = nullptr;
+    if (jitter_x || jitter_v) {
+        CK(cudaMallocAsync((void **)&dj, sizeof(double) * 2 * n, ctx->stream));
+        if (jitter_x) CK(cudaMemcpyAsync(dj, jitter_x, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+        else CK(cudaMemsetAsync(dj, 0, sizeof(double) * n, ctx->stream));
+        if (jitter_v) CK(cudaMemcpyAsync(dj + n, jitter_v, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+        else CK(cudaMemsetAsync(dj + n, 0, sizeof(double) * n, ctx->stream));
+    }
+    const int64_t p0 = ctx->off[run];
+    CK(launch_init_lattice(ctx->prec, ctx->dec, ctx->st[0], ctx->st[1], ctx->st[2], ctx->st[3],
+                           ctx->st[4], p0, ctx->cfg[run].L, lat, dj, dj ? dj + n : nullptr,
+                           ctx->stream));
+    ctx->launches += 2;
+    if (dj) CK(cudaFreeAsync(dj, ctx->stream));
+    ctx->prepared = false;
+    return SWPIC_OK;
+}
+
+swpic_status swpic_refresh(swpic_ctx *ctx) { return prepare(ctx, false); }
+
+swpic_status swpic_deposit(swpic_ctx *ctx) {
+    swpic_status s = ensure_prepared(ctx);
+    if (s != SWPIC_OK) return s;
+    CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
+    s = enqueue_pass(ctx, 0.0, 0.0, 0.0, PASS_DEPOSIT | PASS_NO_WRITE, false);
+    if (s != SWPIC_OK) return s;
+    PassArgs b = base_args(ctx);
+    b.flags = 0;   // neutralise only: b, btilde; acc kept for solve_field
+    CK(launch_solve_runs(ctx->prec, b, 256, solve_smem_bytes(ctx->max_nx), ctx->stream));
+    ctx->launches += 1;
+    return SWPIC_OK;
+}
+
+swpic_status swpic_solve_field(swpic_ctx *ctx) {
+    swpic_status s = ensure_prepared(ctx);
+    if (s != SWPIC_OK) return s;
+    PassArgs b = base_args(ctx);
+    b.flags = PASS_SOLVE;
+    CK(launch_solve_runs(ctx->prec, b, 256, solve_smem_bytes(ctx->max_nx), ctx->stream));
+    ctx->launches += 1;
+    return SWPIC_OK;
+}
+
+swpic_status swpic_gather_push(swpic_ctx *ctx, double kick_fraction, double drift_fraction) {
+    swpic_status s = ensure_prepared(ctx);
+    if (s != SWPIC_OK) return s;
+    if (!std::isfinite(kick_fraction) || !std::isfinite(drift_fraction))
+        return fail(ctx, SWPIC_EINVAL, "fractions must be finite");
+    return enqueue_pass(ctx, 0.0, kick_fraction, drift_fraction, 0u, false);
+}
+
+swpic_status swpic_sort(swpic_ctx *ctx) {
+    swpic_status s = ensure_prepared(ctx);
+    if (s != SWPIC_OK) return s;
+    if (!ctx->scratch) return fail(ctx, SWPIC_ESTATE, "sorting needs scratch (see swpic_scratch_bytes)");
+    s = enqueue_sort(ctx);
+    if (s != SWPIC_OK) return s;
+    const size_t bytes = (size_t)ctx->N * elem_size(ctx->prec);
+    for (int k = 0; k < 5; ++k)
+        if (ctx->st[k] && ctx->sc[k] && bytes)
+            CK(cudaMemcpyAsync(ctx->st[k], ctx->sc[k], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    return SWPIC_OK;
+}
+
+swpic_status swpic_step(swpic_ctx *ctx, int32_t n_steps, int32_t diag_every) {
+    swpic_status s = ensure_prepared(ctx);
+    if (s != SWPIC_OK) return s;
+    if (n_steps < 0) return fail(ctx, SWPIC_EINVAL, "n_steps must be >= 0");
+    if (n_steps == 0) return SWPIC_OK;
+    const std::vector<Op> ops = build_ops(ctx, n_steps, diag_every);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(ctx->stream, &cap));
+    const bool use_graph = ctx->graphs && cap == cudaStreamCaptureStatusNone && ctx->stream != nullptr;
+    int npass = 0;
+    if (use_graph) {
+        const std::string key = ops_key(ctx, ops);
+        auto it = ctx->graph_cache.find(key);
+        if (it == ctx->graph_cache.end()) {
+            if (ctx->graph_cache.size() >= 16) clear_graphs(ctx);
+            if (ctx->timing) { s = ensure_events(ctx, 2 * (size_t)(n_steps + 1)); if (s != SWPIC_OK) return s; }
+            CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            GraphEntry ge;
+            const int64_t l0 = ctx->launches;
+            s = enqueue_ops(ctx, ops, &ge.kernels, &ge.n_passes);
+            ctx->launches = l0;
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+            if (s != SWPIC_OK) { if (g) cudaGraphDestroy(g); return s; }
+            if (e != cudaSuccess) return fail_cuda(ctx, "cudaStreamEndCapture", e);
+            e = cudaGraphInstantiate(&ge.exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail_cuda(ctx, "cudaGraphInstantiate", e);
+            it = ctx->graph_cache.emplace(key, ge).first;
+        }
+        CK(cudaGraphLaunch(it->second.exec, ctx->stream));
+        ctx->launches += it->second.kernels;
+        npass = it->second.n_passes;
+    } else {
+        s = enqueue_ops(ctx, ops, nullptr, &npass);
+        if (s != SWPIC_OK) return s;
+    }
+    ctx->n_timed = ctx->timing ? npass : 0;
+    // the last record written is at the highest diag step of this call
+    {
+        int64_t st = ctx->step;
+        for (const Op &o : ops) {
+            if (o.kind != 0) continue;
+            if (o.flags & PASS_DIAG) ctx->last_diag_step = st;
+            if (o.flags & PASS_COUNT_STEP) ++st;
+        }
+    }
+    ctx->step += n_steps;
+    return SWPIC_OK;
+}
+
+swpic_status swpic_synchronize(swpic_ctx *ctx) {
+    if (!ctx) return SWPIC_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    int32_t e = 0;
+    CK(cudaMemcpy(&e, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (e) {
+        cudaMemset(ctx->d_err, 0, sizeof(int32_t));
+        return fail(ctx, SWPIC_ENUMERIC, (e & kErrFixedOverflow) ? "charge accumulator overflow"
+                                                                 : "non-finite field");
+    }
+    return SWPIC_OK;
+}
+
+swpic_status swpic_diagnostics(swpic_ctx *ctx, int32_t run, swpic_diag *out, int32_t max_records,
+                               int32_t *n_records) {
+    if (!ctx || !n_records || max_records < 0 || (max_records > 0 && !out)) return SWPIC_EINVAL;
+    if (run < 0 || run >= ctx->R) return fail(ctx, SWPIC_EINVAL, "bad run");
+    swpic_status s = ensure_prepared(ctx);
+    if (s != SWPIC_OK) return s;
+    s = swpic_synchronize(ctx);
+    if (s != SWPIC_OK) return s;
+    int32_t cnt = 0;
+    CK(cudaMemcpy(&cnt, ctx->d_ring_count + run, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    const int32_t have = std::min(cnt, ctx->cap);
+    const int32_t take = std::min(have, max_records);
+    std::vector<double> buf((size_t)ctx->cap * kDiagWords);
+    CK(cudaMemcpy(buf.data(), ctx->d_ring + (size_t)run * ctx->cap * kDiagWords,
+                  sizeof(double) * kDiagWords * ctx->cap, cudaMemcpyDeviceToHost));
+    const int32_t first = cnt - have;   // oldest record kept
+    for (int32_t k = 0; k < take; ++k) {
+        const double *rec = &buf[(size_t)((first + k) % ctx->cap) * kDiagWords];
+        swpic_diag &d = out[k];
+        d.t = rec[0]; d.mass = rec[1]; d.momentum = rec[2]; d.kinetic = rec[3];
+        d.field_energy = rec[4]; d.hamiltonian = rec[5]; d.e_amp = rec[6]; d.step = (int64_t)rec[7];
+    }
+    *n_records = take;
+    return SWPIC_OK;
+}
+
+swpic_status swpic_get_mesh(swpic_ctx *ctx, int32_t run, double *b, double *btilde, double *Phi,
+                            double *E, double *d2) {
+    if (!ctx) return SWPIC_EINVAL;
+    if (run < 0 || run >= ctx->R) return fail(ctx, SWPIC_EINVAL, "bad run");
+    swpic_status s = ensure_prepared(ctx);
+    if (s != SWPIC_OK) return s;
+    const int nx = ctx->nx[run], mo = ctx->mesh_off[run];
+    if (Phi) {
+        CK(launch_phi(ctx->d_runs, ctx->R, ctx->d_e, ctx->d_phi, ctx->max_nx, ctx->stream));
+        ctx->launches += 1;
+    }
+    s = swpic_synchronize(ctx);
+    if (s != SWPIC_OK) return s;
+    if (b) CK(cudaMemcpy(b, ctx->d_b + mo, sizeof(double) * nx, cudaMemcpyDeviceToHost));
+    if (btilde) CK(cudaMemcpy(btilde, ctx->d_bt + mo, sizeof(double) * nx, cudaMemcpyDeviceToHost));
+    if (Phi) CK(cudaMemcpy(Phi, ctx->d_phi + mo, sizeof(double) * nx, cudaMemcpyDeviceToHost));
+    if (E) CK(cudaMemcpy(E, ctx->d_e + mo, sizeof(double) * nx, cudaMemcpyDeviceToHost));
+    if (d2) {
+        const size_t es = elem_size(ctx->prec);
+        std::vector<unsigned char> t((size_t)nx * 2 * es);
+        CK(cudaMemcpy(t.data(), (char *)ctx->d_table + (size_t)mo * 2 * es, t.size(), cudaMemcpyDeviceToHost));
+        for (int j = 0; j < nx; ++j) {
+            if (es == 8) d2[j] = reinterpret_cast<const double *>(t.data())[2 * j + 1];
+            else d2[j] = reinterpret_cast<const float *>(t.data())[2 * j + 1];
+        }
+    }
+    return SWPIC_OK;
+}
+
+swpic_status swpic_get_keys(swpic_ctx *ctx, int32_t *keys, int64_t n) {
+    swpic_status s = check_bound(ctx);
+    if (s != SWPIC_OK) return s;
+    if (n != ctx->N || (n > 0 && !keys)) return fail(ctx, SWPIC_EINVAL, "n must equal the particle count");
+    if (n == 0) return SWPIC_OK;
+    int32_t *dk = nullptr;
+    CK(cudaMallocAsync((void **)&dk, sizeof(int32_t) * n, ctx->stream));
+    CK(launch_keys(ctx->prec, ctx->st[0], ctx->d_runs, ctx->R, n, dk, ctx->stream));
+    ctx->launches += 1;
+    CK(cudaMemcpyAsync(keys, dk, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaFreeAsync(dk, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return SWPIC_OK;
+}
+
+swpic_status swpic_step_host(swpic_ctx *ctx, const void *Q, const void *P, const void *qs,
+                             const void *ps, const void *psi, void *Q_out, void *P_out,
+                             void *qs_out, void *ps_out, int64_t n, int32_t n_steps,
+                             int32_t diag_every) {
+    swpic_status s = check_bound(ctx);
+    if (s != SWPIC_OK) return s;
+    if (n != ctx->N) return fail(ctx, SWPIC_EINVAL, "n must equal the total particle count");
+    const size_t bytes = (size_t)n * elem_size(ctx->prec);
+    const void *src[5] = {Q, P, qs, ps, psi};
+    if (n > 0) {
+        for (int k = 0; k < 5; ++k) {
+            if (!ctx->st[k]) continue;
+            if (src[k]) CK(cudaMemcpyAsync(ctx->st[k], src[k], bytes, cudaMemcpyHostToDevice, ctx->stream));
+            else CK(cudaMemsetAsync(ctx->st[k], 0, bytes, ctx->stream));
+        }
+    }
+    s = prepare(ctx, false);
+    if (s != SWPIC_OK) return s;
+    s = swpic_step(ctx, n_steps, diag_every);
+    if (s != SWPIC_OK) return s;
+    void *dst[4] = {Q_out, P_out, qs_out, ps_out};
+    if (n > 0)
+        for (int k = 0; k < 4; ++k)
+            if (dst[k] && ctx->st[k])
+                CK(cudaMemcpyAsync(dst[k], ctx->st[k], bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    return swpic_synchronize(ctx);
+}
+
+// ---- checkpoint -----------------------------------------------------------
+static const char kMagic[8] = {'S', 'W', 'P', 'I', 'C', 'v', '1', 0};
+
+swpic_status swpic_save(swpic_ctx *ctx, const char *path) {
+    swpic_status s = ensure_prepared(ctx);
+    if (s != SWPIC_OK) return s;
+    if (!path) return fail(ctx, SWPIC_EINVAL, "null path");
+    s = swpic_synchronize(ctx);
+    if (s != SWPIC_OK) return s;
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, SWPIC_EIO, std::string("cannot open ") + path);
+    const size_t es = elem_size(ctx->prec);
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
+    int32_t hdr[4] = {ctx->R, ctx->prec, ctx->dec ? 1 : 0, 0};
+    ok &= std::fwrite(hdr, sizeof(hdr), 1, f) == 1;
+    ok &= std::fwrite(&ctx->N, sizeof(int64_t), 1, f) == 1;
+    ok &= std::fwrite(&ctx->step, sizeof(int64_t), 1, f) == 1;
+    for (int r = 0; r < ctx->R; ++r) {
+        double g[2] = {ctx->cfg[r].L, ctx->cfg[r].dt};
+        int32_t nx = ctx->cfg[r].nx;
+        ok &= std::fwrite(g, sizeof(g), 1, f) == 1;
+        ok &= std::fwrite(&nx, sizeof(nx), 1, f) == 1;
+        ok &= std::fwrite(&ctx->off[r + 1], sizeof(int64_t), 1, f) == 1;
+    }
+    std::vector<long long> steps(ctx->R);
+    cudaMemcpy(steps.data(), ctx->d_steps, sizeof(long long) * ctx->R, cudaMemcpyDeviceToHost);
+    ok &= std::fwrite(steps.data(), sizeof(long long), ctx->R, f) == (size_t)ctx->R;
+    std::vector<unsigned char> buf((size_t)ctx->N * es);
+    for (int k = 0; k < 5 && ok; ++k) {
+        if (!ctx->st[k]) continue;
+        if (ctx->N) {
+            cudaError_t e = cudaMemcpy(buf.data(), ctx->st[k], buf.size(), cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) { std::fclose(f); return fail_cuda(ctx, "save", e); }
+        }
+        ok &= std::fwrite(buf.data(), 1, buf.size(), f) == buf.size();
+    }
+    ok &= std::fclose(f) == 0;
+    if (!ok) return fail(ctx, SWPIC_EIO, std::string("write failed: ") + path);
+    return SWPIC_OK;
+}
+
+swpic_status swpic_load(swpic_ctx *ctx, const char *path) {
+    swpic_status s = check_bound(ctx);
+    if (s != SWPIC_OK) return s;
+    if (!path) return fail(ctx, SWPIC_EINVAL, "null path");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, SWPIC_EIO, std::string("cannot open ") + path);
+    auto bad = [&](const char *why) { std::fclose(f); return fail(ctx, SWPIC_EIO, why); };
+    char magic[8];
+    int32_t hdr[4];
+    int64_t N = 0, step = 0;
+    if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMagic, 8) != 0) return bad("not a checkpoint");
+    if (std::fread(hdr, sizeof(hdr), 1, f) != 1 || std::fread(&N, 8, 1, f) != 1 || std::fread(&step, 8, 1, f) != 1)
+        return bad("truncated header");
+    if (hdr[0] != ctx->R || hdr[1] != ctx->prec || hdr[2] != (ctx->dec ? 1 : 0) || N != ctx->N)
+        return bad("checkpoint does not match the context configuration");
+    for (int r = 0; r < ctx->R; ++r) {
+        double g[2];
+        int32_t nx;
+        int64_t o;
+        if (std::fread(g, sizeof(g), 1, f) != 1 || std::fread(&nx, 4, 1, f) != 1 || std::fread(&o, 8, 1, f) != 1)
+            return bad("truncated run table");
+        if (g[0] != ctx->cfg[r].L || g[1] != ctx->cfg[r].dt || nx != ctx->cfg[r].nx || o != ctx->off[r + 1])
+            return bad("checkpoint run geometry differs");
+    }
+    std::vector<long long> steps(ctx->R);
+    if (std::fread(steps.data(), sizeof(long long), ctx->R, f) != (size_t)ctx->R) return bad("truncated steps");
+    const size_t es = elem_size(ctx->prec);
+    std::vector<unsigned char> buf((size_t)ctx->N * es);
+    for (int k = 0; k < 5; ++k) {
+        if (!ctx->st[k]) continue;
+        if (std::fread(buf.data(), 1, buf.size(), f) != buf.size()) return bad("truncated state");
+        if (ctx->N) {
+            cudaError_t e = cudaMemcpy(ctx->st[k], buf.data(), buf.size(), cudaMemcpyHostToDevice);
+            if (e != cudaSuccess) { std::fclose(f); return fail_cuda(ctx, "load", e); }
+        }
+    }
+    std::fclose(f);
+    CK(cudaMemcpy(ctx->d_steps, steps.data(), sizeof(long long) * ctx->R, cudaMemcpyHostToDevice));
+    CK(cudaMemset(ctx->d_ring_count, 0, sizeof(int32_t) * ctx->R));
+    ctx->step = step;
+    return prepare(ctx, true);
+}
+
+// ---- launch shape, tuning, measurement ----------------------------------------
+swpic_status swpic_set_launch(swpic_ctx *ctx, int32_t tpb, int32_t bpsm, int32_t resort) {
+    if (!ctx) return SWPIC_EINVAL;
+    if (tpb != 0 && (tpb < 64 || tpb > 512 || tpb % 32)) return fail(ctx, SWPIC_EINVAL, "bad threads_per_block");
+    if (bpsm < 0 || bpsm > 32) return fail(ctx, SWPIC_EINVAL, "bad blocks_per_sm");
+    if (resort < 0) return fail(ctx, SWPIC_EINVAL, "bad resort_every");
+    if (tpb) ctx->tpb = tpb;
+    if (bpsm) ctx->bpsm = bpsm;
+    ctx->resort = resort;
+    clear_graphs(ctx);
+    return SWPIC_OK;
+}
+
+swpic_status swpic_get_launch(const swpic_ctx *ctx, int32_t *tpb, int32_t *bpsm, int32_t *resort) {
+    if (!ctx) return SWPIC_EINVAL;
+    if (tpb) *tpb = ctx->tpb;
+    if (bpsm) *bpsm = ctx->bpsm;
+    if (resort) *resort = ctx->resort;
+    return SWPIC_OK;
+}
+
+swpic_status swpic_set_timing(swpic_ctx *ctx, int32_t enable) {
+    if (!ctx) return SWPIC_EINVAL;
+    ctx->timing = enable != 0;
+    clear_graphs(ctx);
+    return SWPIC_OK;
+}
+
+swpic_status swpic_pass_times(swpic_ctx *ctx, float *ms, int32_t max_passes, int32_t *n_passes) {
+    if (!ctx || !n_passes || (max_passes > 0 && !ms)) return SWPIC_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int n = std::min(ctx->n_timed, max_passes);
+    for (int k = 0; k < n; ++k) CK(cudaEventElapsedTime(&ms[k], ctx->events[2 * k], ctx->events[2 * k + 1]));
+    *n_passes = n;
+    return SWPIC_OK;
+}
+
+swpic_status swpic_launch_count(const swpic_ctx *ctx, int64_t *count) {
+    if (!ctx || !count) return SWPIC_EINVAL;
+    *count = ctx->launches;
+    return SWPIC_OK;
+}
+
+// Autotuner: threads per block x blocks per SM x re-sort interval, timed with
+// CUDA events on the bound state, which is restored bit for bit afterwards.
+swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char *cache_path) {
+    swpic_status s = ensure_prepared(ctx);
+    if (s != SWPIC_OK) return s;
+    if (steps_per_trial <= 0) return fail(ctx, SWPIC_EINVAL, "steps_per_trial must be > 0");
+    char key[512];
+    std::snprintf(key, sizeof(key), "%s|f%d|dec%d|mode%d|runs%d|n%lld|mesh%d", ctx->gpu_name.c_str(),
+                  ctx->prec, ctx->dec ? 1 : 0, ctx->mode, ctx->R, (long long)ctx->N, ctx->total_mesh);
+    std::string text;
+    if (cache_path) {
+        if (FILE *f = std::fopen(cache_path, "rb")) {
+            char buf[4096];
+            size_t k;
+            while ((k = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, k);
+            std::fclose(f);
+        }
+        const std::string needle = std::string("\"") + key + "\"";
+        const size_t at = text.find(needle);
+        if (at != std::string::npos) {
+            int tpb = 0, bpsm = 0, rs = -1;
+            const char *p = text.c_str() + at + needle.size();
+            const char *a = std::strstr(p, "\"threads_per_block\":");
+            const char *b = std::strstr(p, "\"blocks_per_sm\":");
+            const char *c = std::strstr(p, "\"resort_every\":");
+            if (a && b && c && std::sscanf(a + 20, "%d", &tpb) == 1 && std::sscanf(b + 16, "%d", &bpsm) == 1 &&
+                std::sscanf(c + 15, "%d", &rs) == 1)
+                return swpic_set_launch(ctx, tpb, bpsm, rs);
+        }
+    }
+    // snapshot what a trial changes
+    const size_t es = elem_size(ctx->prec);
+    const size_t bytes = (size_t)ctx->N * es;
+    std::vector<void *> snap(5, nullptr);
+    for (int k = 0; k < 5; ++k)
+        if (ctx->st[k] && bytes) CK(cudaMalloc(&snap[k], bytes));
+    for (int k = 0; k < 5; ++k)
+        if (snap[k]) CK(cudaMemcpyAsync(snap[k], ctx->st[k], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+    std::vector<long long> steps(ctx->R);
+    std::vector<int32_t> rc(ctx->R);
+    CK(cudaMemcpyAsync(steps.data(), ctx->d_steps, sizeof(long long) * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(rc.data(), ctx->d_ring_count, sizeof(int32_t) * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int64_t step0 = ctx->step, last_diag0 = ctx->last_diag_step;
+    const int tpb0 = ctx->tpb, bpsm0 = ctx->bpsm, rs0 = ctx->resort;
+    auto restore = [&]() -> swpic_status {
+        for (int k = 0; k < 5; ++k)
+            if (snap[k]) CK(cudaMemcpyAsync(ctx->st[k], snap[k], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(ctx->d_steps, steps.data(), sizeof(long long) * ctx->R, cudaMemcpyHostToDevice, ctx->stream));
+        ctx->step = step0;
+        swpic_status q = prepare(ctx, true);
+        if (q != SWPIC_OK) return q;
+        CK(cudaMemcpyAsync(ctx->d_ring_count, rc.data(), sizeof(int32_t) * ctx->R, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        ctx->last_diag_step = last_diag0;
+        return SWPIC_OK;
+    };
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    const int tpbs[] = {128, 256, 512};
+    const int bpsms[] = {1, 2, 4, 8};
+    std::vector<int> rss = {0};
+    if (ctx->scratch) { rss.push_back(5); rss.push_back(20); rss.push_back(50); }
+    float best = 1e30f;
+    int bt = tpb0, bb = bpsm0, br = rs0;
+    swpic_status st = SWPIC_OK;
+    for (int tpb : tpbs) {
+        for (int bpsm : bpsms) {
+            if (tpb * bpsm > 2048) continue;
+            for (int rs : rss) {
+                ctx->tpb = tpb; ctx->bpsm = bpsm; ctx->resort = rs;
+                clear_graphs(ctx);
+                float ms = 0.f;
+                for (int rep = 0; rep < 2 && st == SWPIC_OK; ++rep) {
+                    st = restore();
+                    if (st != SWPIC_OK) break;
+                    cudaEventRecord(e0, ctx->stream);
+                    st = swpic_step(ctx, steps_per_trial, 0);
+                    cudaEventRecord(e1, ctx->stream);
+                    if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, SWPIC_ECUDA, "autotune trial");
+                    cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (st != SWPIC_OK) break;
+                if (ms < best) { best = ms; bt = tpb; bb = bpsm; br = rs; }
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tpb = bt; ctx->bpsm = bb; ctx->resort = br;
+    clear_graphs(ctx);
+    swpic_status rs_ = restore();
+    for (void *p : snap) if (p) cudaFree(p);
+    if (st != SWPIC_OK) return st;
+    if (rs_ != SWPIC_OK) return rs_;
+    if (cache_path) {
+        char line[768];
+        std::snprintf(line, sizeof(line),
+                      " \"%s\": {\"threads_per_block\": %d, \"blocks_per_sm\": %d, \"resort_every\": %d, "
+                      "\"ms_per_step\": %.6g}",
+                      key, bt, bb, br, best / steps_per_trial);
+        std::string body;
+        const size_t open = text.find('{'), close = text.rfind('}');
+        if (open != std::string::npos && close != std::string::npos && close > open) {
+            std::string inner = text.substr(open + 1, close - open - 1);
+            while (!inner.empty() && (inner.back() == '\n' || inner.back() == ' ')) inner.pop_back();
+            body = "{" + inner + (inner.find('"') != std::string::npos ? ",\n" : "\n") + line + "\n}\n";
+        } else {
+            body = std::string("{\n") + line + "\n}\n";
+        }
+        if (FILE *f = std::fopen(cache_path, "wb")) {
+            std::fwrite(body.data(), 1, body.size(), f);
+            std::fclose(f);
+        }
+    }
+    return SWPIC_OK;
+}
+
+}  // extern "C"

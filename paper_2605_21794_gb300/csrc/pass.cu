@@ -1,0 +1,642 @@
+// The particle pass of the decorated-particle step (sm_103a), and the per-run
+// field solve that the last CTA of each run performs at the end of a pass.
+//
+// One pass over the particles of every run does, per particle (Sec. 5,
+// Eq. sw-evolution, with the canonical kick/drift split):
+//   i      = clamp(floor(Q * nx/L), 0, nx-1)                       element of Q
+//   P     -= c1 dt phi_h'_i ;  q* += c1 dt p* phi_h''(Q)           closing half-kick
+//   [diag]  sum psi* P + q*,  sum psi* P^2/2 + q* P                 integer time
+//   P     -= c2 dt phi_h'_i ;  q* += c2 dt p* phi_h''(Q)           opening half-kick
+//   Q      = wrap(Q + cd dt P) ;  p* -= cd dt q*                    drift
+//   [deposit] b_i += psi*(1 - xi) + p*/h,  b_{i+1} += psi* xi - p*/h  (Eq. rhs-assembly)
+// with xi = Q nx/L - i of the drifted Q.  A full leapfrog step in one pass has
+// c1 = c2 = 1/2, cd = 1: the two half-kicks with the same field are applied
+// one after the other, so the pass is bit-for-bit the kick-drift-kick step.
+//
+// Deposit: every thread accumulates the contributions of its consecutive
+// particles while they stay in one element (sorted particles give long runs)
+// and flushes a run into the CTA's shared-memory mesh on an element change.
+// ATOMIC mode flushes float/double shared atomics; DETERMINISTIC mode flushes
+// 64-bit fixed-point integer atomics, which are associative, so the result
+// does not depend on the order in which threads flush.  At the end of its
+// particle range a CTA adds its mesh into the run's global int64 accumulator.
+//
+// The CTA that completes the last particles of a run (a completion counter,
+// no spinning) then removes the mean of b (Eq. neutrality / zero-mean test
+// space), solves A Phi = btilde (Eq. lin-sys) by Gauss's law
+//   e_j - e_{j-1} = btilde_j,  sum_j e_j = 0       (e_i = -phi_h' on element i)
+// and rebuilds the (phi_h', phi_h'') table for the next pass.
+#include <math.h>
+
+#include "swpic_internal.cuh"
+
+namespace swpic {
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+template <typename T> struct Vec16;   // 16-byte vector of T
+template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+
+__device__ __forceinline__ float flo(float x) { return floorf(x); }
+__device__ __forceinline__ double flo(double x) { return floor(x); }
+
+template <typename T> struct Geo { T L, inv_h, inv_L, dt; };
+__device__ __forceinline__ Geo<float> geo_of(const RunDev &r, float) { return {r.Lf, r.inv_hf, r.inv_Lf, r.dtf}; }
+__device__ __forceinline__ Geo<double> geo_of(const RunDev &r, double) { return {r.L, r.inv_h, r.inv_L, r.dt}; }
+
+template <typename T>
+__device__ __forceinline__ int elem_of(T Q, T inv_h, int nx) {
+    int i = (int)flo(Q * inv_h);
+    return max(0, min(nx - 1, i));
+}
+
+// Periodic wrap into [0, L); a value that rounds up to L maps to 0.
+template <typename T>
+__device__ __forceinline__ T wrap_pos(T Q, T L) {
+    if (Q < T(0) || Q >= L) {
+        T k = flo(Q / L);
+        Q = Q - L * k;
+        if (Q >= L) Q -= L;
+        if (Q < T(0)) Q += L;
+    }
+    return Q;
+}
+
+// value * 2^k as an int64 bit pattern; out-of-range (or NaN) sets the error flag
+__device__ __forceinline__ unsigned long long to_fixed(double x, double scale, int32_t *err) {
+    double y = x * scale;
+    if (!(fabs(y) < 4.0e18)) { atomicOr(err, kErrFixedOverflow); return 0ull; }
+    return (unsigned long long)__double2ll_rn(y);
+}
+__device__ __forceinline__ unsigned long long to_fixed(float x, double scale, int32_t *err) {
+    float y = x * (float)scale;   // exact: scale is a power of two
+    if (!(fabsf(y) < 4.0e18f)) { atomicOr(err, kErrFixedOverflow); return 0ull; }
+    return (unsigned long long)__float2ll_rn(y);
+}
+
+// ---------------------------------------------------------------------------
+// block-wide helpers (blockDim.x a multiple of 32, <= 1024)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ long long warp_sum_ll(long long v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_sum_d(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ long long block_sum_ll(long long v, long long *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_ll(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    long long t = 0;
+    for (int k = 0; k < nw; ++k) t += sh[k];
+    return t;
+}
+__device__ double block_sum_d(double v, double *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    v = warp_sum_d(v);
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int k = 0; k < nw; ++k) t += sh[k];   // fixed order: deterministic
+    return t;
+}
+// exclusive scan of one int64 per thread, in thread order
+__device__ long long block_exscan_ll(long long v, long long *sh) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    long long inc = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) sh[w] = inc;
+    __syncthreads();
+    long long base = 0;
+    for (int k = 0; k < w; ++k) base += sh[k];
+    (void)nw;
+    return base + inc - v;
+}
+
+// ---------------------------------------------------------------------------
+// per-run field solve by one CTA (FP64, exact integer neutralisation)
+// full = false: only b and btilde are written and acc is left as is.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned char *smem, bool full) {
+    using T2 = typename Vec2<T>::type;
+    __shared__ long long sh_ll[32];
+    __shared__ double sh_d[32];
+    const int nx = R.nx, tid = threadIdx.x, nt = blockDim.x;
+    long long *s_acc = reinterpret_cast<long long *>(smem);
+    double *s_e = reinterpret_cast<double *>(smem + (size_t)a.max_nx * 8);
+    const int per = (nx + nt - 1) / nt;
+    const int j0 = min(nx, tid * per), j1 = min(nx, j0 + per);
+    unsigned long long *acc = a.acc + R.mesh_off;
+    const int off = R.mesh_off;
+
+    long long loc = 0;
+    for (int j = j0; j < j1; ++j) {
+        long long v = (long long)__ldcg(acc + j);
+        s_acc[j] = v;
+        loc += v;
+    }
+    const long long S = block_sum_ll(loc, sh_ll);          // exact (mod 2^64)
+    long long q = S / nx, rem = S % nx;                    // S = q nx + rem, 0 <= rem < nx
+    if (rem < 0) { rem += nx; q -= 1; }
+    const double inv = R.fx_inv;
+    const double rem_node = (double)rem * inv / (double)nx;   // fractional mean per node
+
+    long long tot = 0;
+    for (int j = j0; j < j1; ++j) tot += s_acc[j] - q;
+    long long p = block_exscan_ll(tot, sh_ll);
+    double esum = 0.0;
+    for (int j = j0; j < j1; ++j) {
+        const long long bt = s_acc[j] - q;
+        p += bt;                                           // exact prefix of btilde
+        const double btd = (double)bt * inv - rem_node;
+        a.b[off + j] = (double)s_acc[j] * inv;
+        a.btilde[off + j] = btd;
+        const double er = (double)p * inv - (double)(j + 1) * rem_node;
+        s_e[j] = er;
+        esum += er;
+    }
+    if (!full) return;
+    const double mean_e = block_sum_d(esum, sh_d) / (double)nx;
+    for (int j = j0; j < j1; ++j) s_e[j] -= mean_e;
+    __syncthreads();
+    T2 *tab = reinterpret_cast<T2 *>(a.table) + off;
+    double e2 = 0.0;
+    const double half_inv_h = 0.5 * R.inv_h;
+    for (int j = j0; j < j1; ++j) {
+        const double ej = s_e[j];
+        e2 += ej * ej;
+        a.efield[off + j] = ej;
+        double d2;
+        if (a.d2_mode == SWPIC_D2_NODAL) {
+            const long long bt = s_acc[j] - q;
+            d2 = -((double)bt * inv - rem_node) * R.inv_h;
+        } else {
+            const double em = s_e[j == 0 ? nx - 1 : j - 1];
+            const double ep = s_e[j == nx - 1 ? 0 : j + 1];
+            d2 = (em - ep) * half_inv_h;
+        }
+        T2 t;
+        t.x = (T)(-ej);
+        t.y = (T)d2;
+        tab[j] = t;
+        acc[j] = 0ull;
+    }
+    const double E2 = block_sum_d(e2, sh_d);
+    if (tid == 0) {
+        const double W = 0.5 * R.h * E2;
+        const double Ea = sqrt(E2 / (double)nx);
+        a.field_diag[2 * r] = W;
+        a.field_diag[2 * r + 1] = Ea;
+        if (!isfinite(W)) atomicOr(a.err, kErrNonFinite);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-thread state of a pass
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Kahan {
+    T s, c;
+    __device__ __forceinline__ void add(T x) {
+        T y = x - c;
+        T t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+};
+
+template <typename T, bool DEC, int MODE>
+struct Thread {
+    using T2 = typename Vec2<T>::type;
+    // deposit run
+    int cur;
+    T a0, a1;
+    // diagnostics
+    Kahan<T> mom, kin;
+};
+
+template <typename T, int MODE>
+__device__ __forceinline__ void flush_run(int cur, T a0, T a1, void *mesh, double scale, int32_t *err) {
+    if (cur < 0) return;
+    if (MODE == SWPIC_DEPOSIT_ATOMIC) {
+        T *m = reinterpret_cast<T *>(mesh);
+        atomicAdd(m + cur, a0);
+        atomicAdd(m + cur + 1, a1);
+    } else {
+        unsigned long long *m = reinterpret_cast<unsigned long long *>(mesh);
+        atomicAdd(m + cur, to_fixed(a0, scale, err));
+        atomicAdd(m + cur + 1, to_fixed(a1, scale, err));
+    }
+}
+
+template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
+__device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
+                                         const typename Vec2<T>::type *tab, const int nx,
+                                         const Geo<T> &G, const T k1, const T k2, const T kd,
+                                         Thread<T, DEC, MODE> &th, void *mesh, double scale,
+                                         int32_t *err) {
+    const int i = elem_of(Q, G.inv_h, nx);
+    const auto f = tab[i];
+    T d2 = T(0);
+    if (DEC) {
+        if (D2 == SWPIC_D2_NODAL) {
+            const T xi = Q * G.inv_h - (T)i;
+            const T g1 = tab[i + 1 == nx ? 0 : i + 1].y;
+            d2 = f.y + xi * (g1 - f.y);
+        } else {
+            d2 = f.y;
+        }
+    }
+    // closing half-kick of the previous step
+    P = P - k1 * f.x;
+    if (DEC) qs = qs + k1 * ps * d2;
+    if (DIAG) {
+        th.mom.add(w * P + (DEC ? qs : T(0)));
+        th.kin.add(T(0.5) * w * P * P + (DEC ? qs * P : T(0)));
+    }
+    // opening half-kick of the next step
+    P = P - k2 * f.x;
+    if (DEC) qs = qs + k2 * ps * d2;
+    // drift
+    Q = wrap_pos(Q + kd * P, G.L);
+    if (DEC) ps = ps - kd * qs;
+    if (DEP) {
+        const int i2 = elem_of(Q, G.inv_h, nx);
+        const T xi = Q * G.inv_h - (T)i2;
+        T w0 = w * (T(1) - xi), w1 = w * xi;
+        if (DEC) {
+            const T dq = ps * G.inv_h;
+            w0 += dq;
+            w1 -= dq;
+        }
+        if (i2 == th.cur) {
+            th.a0 += w0;
+            th.a1 += w1;
+        } else {
+            flush_run<T, MODE>(th.cur, th.a0, th.a1, mesh, scale, err);
+            th.cur = i2;
+            th.a0 = w0;
+            th.a1 = w1;
+        }
+    }
+}
+
+__device__ __forceinline__ int find_run(const RunDev *runs, int n_runs, int64_t idx) {
+    int lo = 0, hi = n_runs - 1;
+    while (lo < hi) {                // largest r with p0 <= idx
+        int mid = (lo + hi + 1) >> 1;
+        if (runs[mid].p0 <= idx) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
+__device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, int64_t e,
+                                const typename Vec2<T>::type *s_tab, void *s_mesh,
+                                Thread<T, DEC, MODE> &th) {
+    using V = typename Vec16<T>::type;
+    constexpr int VW = Vec16<T>::n;
+    const Geo<T> G = geo_of(R, T());
+    const int nx = R.nx;
+    const T k1 = (T)(a.c1 * R.dt), k2 = (T)(a.c2 * R.dt), kd = (T)(a.cd * R.dt);
+    const double scale = R.fx_scale;
+    const bool wpsi = (a.flags & PASS_WRITE_PSI) != 0;
+    const T *Qi = reinterpret_cast<const T *>(a.Qi), *Pi = reinterpret_cast<const T *>(a.Pi);
+    const T *qsi = reinterpret_cast<const T *>(a.qsi), *psi = reinterpret_cast<const T *>(a.psi_i);
+    const T *wi = reinterpret_cast<const T *>(a.wi);
+    T *Qo = reinterpret_cast<T *>(a.Qo), *Po = reinterpret_cast<T *>(a.Po);
+    T *qso = reinterpret_cast<T *>(a.qso), *pso = reinterpret_cast<T *>(a.pso);
+    T *wo = reinterpret_cast<T *>(a.wo);
+
+    auto scalar = [&](int64_t k) {
+        T Q = Qi[k], P = Pi[k], w = wi[k];
+        T qs = DEC ? qsi[k] : T(0), ps = DEC ? psi[k] : T(0);
+        push_one<T, DEC, MODE, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, th, s_mesh,
+                                              scale, a.err);
+        Qo[k] = Q;
+        Po[k] = P;
+        if (DEC) { qso[k] = qs; pso[k] = ps; }
+        if (wpsi) wo[k] = w;
+    };
+
+    const int64_t vs = (s + VW - 1) / VW * VW;
+    const int64_t ve = e / VW * VW;
+    if (vs >= ve) {
+        for (int64_t k = s + threadIdx.x; k < e; k += blockDim.x) scalar(k);
+        return;
+    }
+    for (int64_t k = s + threadIdx.x; k < vs; k += blockDim.x) scalar(k);
+    const int64_t v0 = vs / VW, v1 = ve / VW;
+    constexpr int U = 2;
+    const int64_t stride = (int64_t)blockDim.x;
+    int64_t v = v0 + threadIdx.x;
+    for (; v + (U - 1) * stride < v1; v += U * stride) {
+        V q[U], p[U], x[U], y[U], m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int64_t vv = v + u * stride;
+            q[u] = reinterpret_cast<const V *>(Qi)[vv];
+            p[u] = reinterpret_cast<const V *>(Pi)[vv];
+            m[u] = reinterpret_cast<const V *>(wi)[vv];
+            if (DEC) {
+                x[u] = reinterpret_cast<const V *>(qsi)[vv];
+                y[u] = reinterpret_cast<const V *>(psi)[vv];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            T *Q = reinterpret_cast<T *>(&q[u]), *P = reinterpret_cast<T *>(&p[u]);
+            T *X = reinterpret_cast<T *>(&x[u]), *Y = reinterpret_cast<T *>(&y[u]);
+            const T *M = reinterpret_cast<const T *>(&m[u]);
+#pragma unroll
+            for (int l = 0; l < VW; ++l) {
+                T qs = DEC ? X[l] : T(0), ps = DEC ? Y[l] : T(0);
+                push_one<T, DEC, MODE, DEP, DIAG, D2>(Q[l], P[l], qs, ps, M[l], s_tab, nx, G, k1, k2,
+                                                      kd, th, s_mesh, scale, a.err);
+                if (DEC) { X[l] = qs; Y[l] = ps; }
+            }
+            const int64_t vv = v + u * stride;
+            reinterpret_cast<V *>(Qo)[vv] = q[u];
+            reinterpret_cast<V *>(Po)[vv] = p[u];
+            if (DEC) {
+                reinterpret_cast<V *>(qso)[vv] = x[u];
+                reinterpret_cast<V *>(pso)[vv] = y[u];
+            }
+            if (wpsi) reinterpret_cast<V *>(wo)[vv] = m[u];
+        }
+    }
+    for (; v < v1; v += stride) {
+        V q = reinterpret_cast<const V *>(Qi)[v], p = reinterpret_cast<const V *>(Pi)[v];
+        V m = reinterpret_cast<const V *>(wi)[v], x, y;
+        if (DEC) { x = reinterpret_cast<const V *>(qsi)[v]; y = reinterpret_cast<const V *>(psi)[v]; }
+        T *Q = reinterpret_cast<T *>(&q), *P = reinterpret_cast<T *>(&p);
+        T *X = reinterpret_cast<T *>(&x), *Y = reinterpret_cast<T *>(&y);
+        const T *M = reinterpret_cast<const T *>(&m);
+#pragma unroll
+        for (int l = 0; l < VW; ++l) {
+            T qs = DEC ? X[l] : T(0), ps = DEC ? Y[l] : T(0);
+            push_one<T, DEC, MODE, DEP, DIAG, D2>(Q[l], P[l], qs, ps, M[l], s_tab, nx, G, k1, k2, kd,
+                                                  th, s_mesh, scale, a.err);
+            if (DEC) { X[l] = qs; Y[l] = ps; }
+        }
+        reinterpret_cast<V *>(Qo)[v] = q;
+        reinterpret_cast<V *>(Po)[v] = p;
+        if (DEC) { reinterpret_cast<V *>(qso)[v] = x; reinterpret_cast<V *>(pso)[v] = y; }
+        if (wpsi) reinterpret_cast<V *>(wo)[v] = m;
+    }
+    for (int64_t k = ve + threadIdx.x; k < e; k += blockDim.x) scalar(k);
+}
+
+template <typename T>
+__device__ void finish_run(const PassArgs &a, const RunDev &R, int r, unsigned char *smem) {
+    const uint32_t fl = a.flags;
+    if ((fl & PASS_DIAG) && threadIdx.x == 0) {
+        const long long st = a.steps[r];
+        const int32_t cnt = a.ring_count[r];
+        double *rec = a.ring + ((size_t)r * a.ring_cap + (size_t)(cnt % a.ring_cap)) * kDiagWords;
+        const double mom = __ldcg(a.diag_acc + 2 * r), kin = __ldcg(a.diag_acc + 2 * r + 1);
+        const double W = a.field_diag[2 * r], Ea = a.field_diag[2 * r + 1];
+        rec[0] = (double)st * R.dt;
+        rec[1] = a.mass[r];
+        rec[2] = mom;
+        rec[3] = kin;
+        rec[4] = W;
+        rec[5] = kin + W;
+        rec[6] = Ea;
+        rec[7] = (double)st;
+        a.ring_count[r] = cnt + 1;
+        a.diag_acc[2 * r] = 0.0;
+        a.diag_acc[2 * r + 1] = 0.0;
+    }
+    __syncthreads();
+    if (fl & PASS_SOLVE) solve_run<T>(a, R, r, smem, true);
+    if (threadIdx.x == 0) {
+        if (fl & PASS_COUNT_STEP) a.steps[r] += 1;
+        a.run_done[r] = 0ull;
+    }
+}
+
+template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
+__global__ void __launch_bounds__(1024) k_pass(PassArgs a) {
+    using T2 = typename Vec2<T>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_last;
+    __shared__ double s_red[64];
+    T2 *s_tab = reinterpret_cast<T2 *>(smem);
+    void *s_mesh = smem + (size_t)a.max_nx * sizeof(T2);
+
+    const int64_t c0 = (int64_t)blockIdx.x * a.chunk;
+    const int64_t c1 = min(c0 + a.chunk, a.n_total);
+    if (c0 >= c1) return;
+    int r = find_run(a.runs, a.n_runs, c0);
+    int64_t pos = c0;
+    const bool last_work = (a.flags & (PASS_SOLVE | PASS_DIAG | PASS_COUNT_STEP)) != 0;
+    while (pos < c1 && r < a.n_runs) {
+        const RunDev R = a.runs[r];
+        const int64_t s = pos, e = min(c1, R.p1);
+        if (s >= e) { ++r; continue; }
+        const int nx = R.nx;
+        const T2 *gtab = reinterpret_cast<const T2 *>(a.table) + R.mesh_off;
+        for (int j = threadIdx.x; j < nx; j += blockDim.x) s_tab[j] = gtab[j];
+        if (DEP) {
+            if (MODE == SWPIC_DEPOSIT_ATOMIC) {
+                T *m = reinterpret_cast<T *>(s_mesh);
+                for (int j = threadIdx.x; j <= nx; j += blockDim.x) m[j] = T(0);
+            } else {
+                unsigned long long *m = reinterpret_cast<unsigned long long *>(s_mesh);
+                for (int j = threadIdx.x; j <= nx; j += blockDim.x) m[j] = 0ull;
+            }
+        }
+        __syncthreads();
+        Thread<T, DEC, MODE> th;
+        th.cur = -1;
+        th.a0 = th.a1 = T(0);
+        th.mom = {T(0), T(0)};
+        th.kin = {T(0), T(0)};
+        process_segment<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, th);
+        if (DEP) flush_run<T, MODE>(th.cur, th.a0, th.a1, s_mesh, R.fx_scale, a.err);
+        __syncthreads();
+        if (DEP) {
+            unsigned long long *gacc = a.acc + R.mesh_off;
+            for (int j = threadIdx.x; j <= nx; j += blockDim.x) {
+                const int node = (j == nx) ? 0 : j;
+                if (MODE == SWPIC_DEPOSIT_ATOMIC) {
+                    const T v = reinterpret_cast<T *>(s_mesh)[j];
+                    if (v != T(0)) atomicAdd(gacc + node, to_fixed(v, R.fx_scale, a.err));
+                } else {
+                    const unsigned long long v = reinterpret_cast<unsigned long long *>(s_mesh)[j];
+                    if (v != 0ull) atomicAdd(gacc + node, v);
+                }
+            }
+        }
+        if (DIAG) {
+            const double m = warp_sum_d((double)th.mom.s + (double)(-th.mom.c));
+            const double k = warp_sum_d((double)th.kin.s + (double)(-th.kin.c));
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+            if (lane == 0) { s_red[w] = m; s_red[32 + w] = k; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                double sm = 0.0, sk = 0.0;
+                for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { sm += s_red[q]; sk += s_red[32 + q]; }
+                atomicAdd(a.diag_acc + 2 * r, sm);
+                atomicAdd(a.diag_acc + 2 * r + 1, sk);
+            }
+        }
+        if (last_work) {
+            __threadfence();
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                const unsigned long long cnt = (unsigned long long)(e - s);
+                const unsigned long long prev = atomicAdd(a.run_done + r, cnt);
+                s_last = (prev + cnt == (unsigned long long)(R.p1 - R.p0)) ? 1 : 0;
+            }
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                finish_run<T>(a, R, r, smem);
+            }
+        }
+        __syncthreads();
+        pos = e;
+        ++r;
+        while (r < a.n_runs && a.runs[r].p1 <= pos) ++r;
+    }
+}
+
+// solve every run (one CTA per run); used by swpic_solve_field / deposit read-out
+template <typename T>
+__global__ void __launch_bounds__(1024) k_solve_runs(PassArgs a, int full) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int r = blockIdx.x;
+    if (r >= a.n_runs) return;
+    const RunDev R = a.runs[r];
+    solve_run<T>(a, R, r, smem, full != 0);
+}
+
+// Phi from e: Phi_{j+1} = Phi_j - h e_j, then zero mean (one CTA per run)
+__global__ void __launch_bounds__(1024) k_phi(const RunDev *runs, int n_runs, const double *efield,
+                                              double *phi) {
+    __shared__ double sh[32];
+    __shared__ long long shl[32];
+    (void)shl;
+    const int r = blockIdx.x;
+    if (r >= n_runs) return;
+    const RunDev R = runs[r];
+    const int nx = R.nx, nt = blockDim.x, tid = threadIdx.x;
+    const int per = (nx + nt - 1) / nt;
+    const int j0 = min(nx, tid * per), j1 = min(nx, j0 + per);
+    const double *e = efield + R.mesh_off;
+    double *ph = phi + R.mesh_off;
+    // exclusive prefix of -h e (thread-serial + block scan of thread totals)
+    double tot = 0.0;
+    for (int j = j0; j < j1; ++j) tot += -R.h * e[j];
+    const int lane = tid & 31, w = tid >> 5;
+    double inc = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        double y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) sh[w] = inc;
+    __syncthreads();
+    double base = 0.0;
+    for (int k = 0; k < w; ++k) base += sh[k];
+    double p = base + inc - tot, s = 0.0;
+    for (int j = j0; j < j1; ++j) { ph[j] = p; s += p; p += -R.h * e[j]; }
+    __syncthreads();
+    const double mean = block_sum_d(s, sh) / (double)nx;
+    for (int j = j0; j < j1; ++j) ph[j] -= mean;
+}
+
+// ---------------------------------------------------------------------------
+size_t solve_smem_bytes(int max_nx) { return (size_t)max_nx * 16; }
+
+size_t pass_smem_bytes(int prec, int max_nx, int mode) {
+    const size_t t2 = (prec == SWPIC_F64) ? 16 : 8;
+    const size_t me = (mode == SWPIC_DEPOSIT_ATOMIC) ? ((prec == SWPIC_F64) ? 8 : 4) : 8;
+    const size_t push = (size_t)max_nx * t2 + (size_t)(max_nx + 1) * me;
+    const size_t solve = solve_smem_bytes(max_nx);
+    return push > solve ? push : solve;
+}
+
+template <typename T, bool DEC, int MODE>
+static cudaError_t launch_pass_t(const PassArgs &a, int grid, int tpb, size_t smem, cudaStream_t s) {
+    const bool dep = (a.flags & PASS_DEPOSIT) != 0, diag = (a.flags & PASS_DIAG) != 0;
+    const bool nodal = a.d2_mode == SWPIC_D2_NODAL;
+#define SWPIC_LAUNCH(DEP, DIAG, D2)                                                               \
+    do {                                                                                          \
+        auto kern = k_pass<T, DEC, MODE, DEP, DIAG, D2>;                                          \
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                               (int)smem);                                        \
+        if (err != cudaSuccess) return err;                                                       \
+        kern<<<grid, tpb, smem, s>>>(a);                                                          \
+        return cudaGetLastError();                                                                \
+    } while (0)
+    if (nodal) {
+        if (dep && diag) SWPIC_LAUNCH(true, true, SWPIC_D2_NODAL);
+        if (dep) SWPIC_LAUNCH(true, false, SWPIC_D2_NODAL);
+        if (diag) SWPIC_LAUNCH(false, true, SWPIC_D2_NODAL);
+        SWPIC_LAUNCH(false, false, SWPIC_D2_NODAL);
+    } else {
+        if (dep && diag) SWPIC_LAUNCH(true, true, SWPIC_D2_LUMPED);
+        if (dep) SWPIC_LAUNCH(true, false, SWPIC_D2_LUMPED);
+        if (diag) SWPIC_LAUNCH(false, true, SWPIC_D2_LUMPED);
+        SWPIC_LAUNCH(false, false, SWPIC_D2_LUMPED);
+    }
+#undef SWPIC_LAUNCH
+}
+
+cudaError_t launch_pass(int prec, bool decorated, int mode, const PassArgs &a, int grid, int tpb,
+                        size_t smem, cudaStream_t s) {
+    if (prec == SWPIC_F64) {
+        if (decorated) {
+            if (mode == SWPIC_DEPOSIT_ATOMIC) return launch_pass_t<double, true, 0>(a, grid, tpb, smem, s);
+            return launch_pass_t<double, true, 1>(a, grid, tpb, smem, s);
+        }
+        if (mode == SWPIC_DEPOSIT_ATOMIC) return launch_pass_t<double, false, 0>(a, grid, tpb, smem, s);
+        return launch_pass_t<double, false, 1>(a, grid, tpb, smem, s);
+    }
+    if (decorated) {
+        if (mode == SWPIC_DEPOSIT_ATOMIC) return launch_pass_t<float, true, 0>(a, grid, tpb, smem, s);
+        return launch_pass_t<float, true, 1>(a, grid, tpb, smem, s);
+    }
+    if (mode == SWPIC_DEPOSIT_ATOMIC) return launch_pass_t<float, false, 0>(a, grid, tpb, smem, s);
+    return launch_pass_t<float, false, 1>(a, grid, tpb, smem, s);
+}
+
+cudaError_t launch_solve_runs(int prec, const PassArgs &a, int tpb, size_t smem, cudaStream_t s) {
+    const int full = (a.flags & PASS_SOLVE) ? 1 : 0;
+    if (prec == SWPIC_F64) {
+        cudaError_t err = cudaFuncSetAttribute(k_solve_runs<double>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        k_solve_runs<double><<<a.n_runs, tpb, smem, s>>>(a, full);
+    } else {
+        cudaError_t err = cudaFuncSetAttribute(k_solve_runs<float>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        k_solve_runs<float><<<a.n_runs, tpb, smem, s>>>(a, full);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_phi(const RunDev *runs, int n_runs, const double *efield, double *phi, int max_nx,
+                       cudaStream_t s) {
+    (void)max_nx;
+    k_phi<<<n_runs, 256, 0, s>>>(runs, n_runs, efield, phi);
+    return cudaGetLastError();
+}
+
+}  // namespace swpic
