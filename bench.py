@@ -1,0 +1,446 @@
+#!/usr/bin/env python3
+"""Benchmark of the decorated-particle (Scovel-Weinstein, k = 2) step on GB300.
+
+Prints ONE JSON line.  Default workload: bump-on-tail at bandwidth-roofline
+scale, 4096 x 4096 lattice = 16,777,216 decorated particles, nx 1024, dt 0.05,
+FP32 particle state, FP64 Poisson normalisation and compensated energy sums
+(diagnostics every step).  A step is one pass of the whole hot path: element
+keys, the stable sort (at the autotuned cadence), the fused push + deposit,
+the per-run neutralisation + solve + table rebuild, and the diagnostics.
+
+  python bench.py [--steps K] [--warmup W] [--impl ours|reference] [--gpus N]
+
+--impl reference times the FP64 CPU oracle on the host cores (each step one
+oracle step on a bounded sample of the same workload).  Under torchrun
+(N > 1) every rank advances its own independent replica (weak scaling, no
+collective on the data path); the time is the maximum over ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+METRIC = "decorated particle-steps/s & % HBM roofline; batched vs plain at equal error"
+UNIT = "decorated particle-steps/s"
+# algorithmic bytes per particle-step of the fused pass: read Q,P,q*,p*,psi*, write Q,P,q*,p*
+BYTES_PER_PARTICLE = {(32, True): 36, (64, True): 72, (32, False): 20, (64, False): 40}
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=100)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--deposit-mode", choices=["atomic", "deterministic"], default="atomic")
+    ap.add_argument("--diag-every", type=int, default=1)
+    ap.add_argument("--resort", type=int, default=-1, help="-1: autotune")
+    ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the deterministic-mode, e2e, ensemble and CPU-baseline legs")
+    ap.add_argument("--side", type=int, default=4096, help="lattice side (4096 = the workload)")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (no MEASURED_PEAKS.json)"
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ["clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.hw_slowdown",
+              "clocks_event_reasons.hw_thermal_slowdown", "clocks_event_reasons.sw_thermal_slowdown",
+              "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f,
+                stderr=subprocess.DEVNULL)
+            time.sleep(0.15)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.05)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) != len(self.FIELDS):
+                continue
+            try:
+                rows.append((float(parts[0]), float(parts[1]), float(parts[2]), parts[3:]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return None
+        smax = max(r[1] for r in rows)
+        pmax = max(r[2] for r in rows)
+        loaded = [r for r in rows if r[2] > 0.5 * pmax] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in loaded for i, v in enumerate(r[3]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded), "sm_max_mhz": smax,
+                "power_w_max": pmax, "samples": len(rows), "samples_under_load": len(loaded),
+                "reasons": reasons}
+
+
+def gpu_index_for_smi(torch, dev):
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        if vis:
+            return vis.split(",")[dev]
+        return dev
+
+
+# --------------------------------------------------------------------------
+# oracle legs (host cores)
+# --------------------------------------------------------------------------
+def oracle_sample_spec(spec, cols):
+    """The workload with `cols` lattice columns instead of all: same domain,
+    velocity lattice, mesh and dt, fewer particles (a bounded CPU sample)."""
+    import dataclasses
+    return dataclasses.replace(spec.lattice, nq=cols)
+
+
+def time_oracle(spec, cols, steps, warmup, diag_every):
+    import oracle as O
+    lat = oracle_sample_spec(spec, cols)
+    st = O.init_lattice(lat)
+    if warmup > 0:
+        st = O.run(st, spec.nx, lat.L, spec.dt, warmup, diag_every=diag_every)
+    t0 = time.perf_counter()
+    O.run(st, spec.nx, lat.L, spec.dt, steps, diag_every=diag_every)
+    dt = time.perf_counter() - t0
+    return lat.n, dt
+
+
+def run_reference(args, spec):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return
+    cols = max(1, min(spec.lattice.nq, 16))           # 16 x 4096 = 65,536 particles per step
+    n, dt = time_oracle(spec, cols, args.steps, args.warmup, args.diag_every)
+    value = n * args.steps / dt
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(spec, args, None),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d of %d lattice columns (%d particles) of %s, %d steps, "
+                                       "single-threaded plain-C FP64 oracle" %
+                                       (cols, spec.lattice.nq, n, spec.name, args.steps)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(spec, args, resort):
+    return {"workload": spec.name, "particles": spec.lattice.n, "lattice": [spec.lattice.nq, spec.lattice.nv],
+            "nx": spec.nx, "dt": spec.dt, "L": spec.lattice.L, "precision": "fp32 state, fp64 solve",
+            "deposit_mode": args.deposit_mode, "diag_every": args.diag_every,
+            "resort_every": resort,
+            "l2": "inputs larger than L2 (FP32 state %.0f MB > 129 MB)" % (spec.lattice.n * 20 / 1e6),
+            "parallelism": "replicas (one independent run per GPU)"}
+
+
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    spec = W.bump_on_tail(precision=32, side=args.side) if args.side != 4096 else W.bump_on_tail()
+    if args.impl == "reference":
+        run_reference(args, spec)
+        return
+    import torch
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2605_21794_gb300 import build, swpic
+    build.build()
+    lat = spec.lattice
+    n = lat.n
+    mode = 1 if args.deposit_mode == "deterministic" else 0
+
+    def make(mode_, resort, graphs=True):
+        s = swpic.Simulation([(lat.L, spec.dt, spec.nx, n)], precision=32, deposit_mode=mode_,
+                             resort_every=max(resort, 0), use_graphs=graphs, diag_capacity=64)
+        s.init_lattice(0, lat)
+        swpic.swpic_refresh(s.ctx)
+        return s
+
+    sim = make(mode, args.resort)
+    # every leg starts from the initial state: the decorations of this workload
+    # grow without bound late in the run, so no leg runs past
+    # warm-up + K steps from t = 0
+    torch.cuda.synchronize()
+    init_state = [t.clone() for t in (sim.Q, sim.P, sim.qs, sim.ps, sim.psi)]
+
+    def restore(s):
+        torch.cuda.synchronize()
+        for dst, src in zip((s.Q, s.P, s.qs, s.ps, s.psi), init_state):
+            dst.copy_(src)
+        torch.cuda.synchronize()
+        swpic.swpic_refresh(s.ctx)
+
+    if args.resort < 0 and not args.no_autotune:
+        swpic.swpic_autotune(sim.ctx, 10, None)
+    tpb, bpsm, resort = swpic.swpic_get_launch(sim.ctx)
+    restore(sim)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    def timed(s, k):
+        barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        s.step(k, args.diag_every)
+        e1.record(s.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        barrier()
+        return ms
+
+    # warm-up (also captures the step graphs)
+    sim.step(args.warmup, args.diag_every)
+    swpic.swpic_synchronize(sim.ctx)
+    l0 = swpic.swpic_launch_count(sim.ctx)
+    sampler = ClockSampler(gpu_index_for_smi(torch, local)) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    ms = timed(sim, args.steps)
+    clocks = sampler.stop() if sampler else None
+    launches = swpic.swpic_launch_count(sim.ctx) - l0
+    swpic.swpic_synchronize(sim.ctx)
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n * args.steps / (ms / 1e3)
+
+    # per-pass device durations (CUDA events on the context stream, plain launches),
+    # over the same warm-up + K steps from the initial state
+    restore(sim)
+    sim.step(args.warmup, args.diag_every)
+    swpic.swpic_set_timing(sim.ctx, 1)
+    sim.step(args.steps, args.diag_every)
+    pass_ms = swpic.swpic_pass_times(sim.ctx)
+    swpic.swpic_set_timing(sim.ctx, 0)
+    full = pass_ms[1:-1] if len(pass_ms) > 2 else pass_ms
+    avg_pass_ms = float(np.mean(full))
+    bpp = BYTES_PER_PARTICLE[(32, True)]
+    achieved = bpp * n / (avg_pass_ms / 1e3) / 1e9
+    peak, peak_src = measured_peak()
+    traffic = profiled_traffic()
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": traffic,
+                "kernel": "k_pass<float, decorated, %s, deposit, diag>" % args.deposit_mode,
+                "algorithmic_bytes_per_launch": bpp * n,
+                "avg_launch_ms": avg_pass_ms, "peak_source": peak_src,
+                "step_frac": (bpp * n * world / (ms / args.steps / 1e3) / 1e9) / peak}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(spec, args, resort),
+                           launch={"threads_per_block": tpb, "blocks_per_sm": bpsm}),
+            "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
+
+    if not args.no_extras and rank == 0:
+        # deterministic deposit mode, same workload
+        other = 1 - mode
+        s2 = make(other, resort)
+        swpic.swpic_set_launch(s2.ctx, tpb, bpsm, resort)
+        s2.step(args.warmup, args.diag_every)
+        ms2 = timed(s2, args.steps)
+        line["other_deposit_mode"] = {
+            "deposit_mode": "deterministic" if other == 1 else "atomic",
+            "value": n * args.steps / (ms2 / 1e3), "ms_per_step": ms2 / args.steps}
+        s2.close()
+        restore(sim)
+        line["e2e"] = e2e_leg(torch, swpic, sim, n, args)
+        line["batched_vs_plain"] = ensemble_leg(torch, swpic)
+        line["cpu_baseline"] = cpu_baseline_leg(spec, args)
+    elif rank == 0:
+        restore(sim)
+        line["e2e"] = e2e_leg(torch, swpic, sim, n, args)
+    sim.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def profiled_traffic():
+    """DRAM bytes per launch of the fused pass from the committed ncu summary,
+    valid only while the kernel source is the one that was profiled."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2605_21794_gb300", "csrc", "pass.cu")
+    summ = os.path.join(ROOT, "profiles", "k_pass_bump_on_tail_4096.json")
+    try:
+        with open(summ) as f:
+            d = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        if d.get("pass_cu_sha256") == h:
+            return d.get("dram_bytes_per_launch_full_size")
+    except Exception:
+        pass
+    return None
+
+
+def e2e_leg(torch, swpic, sim, n, args):
+    """The same K steps through swpic_step_host: pinned host state in, final
+    state out, copies inside the timed region."""
+    st = sim.state()
+    hin = {k: torch.from_numpy(st[k].astype(np.float32)).pin_memory() for k in ("Q", "P", "qs", "ps", "psi")}
+    hout = {k: torch.empty(n, dtype=torch.float32).pin_memory() for k in ("Q", "P", "qs", "ps")}
+    p = lambda t: t.data_ptr()
+    swpic.swpic_step_host(sim.ctx, p(hin["Q"]), p(hin["P"]), p(hin["qs"]), p(hin["ps"]), p(hin["psi"]),
+                          p(hout["Q"]), p(hout["P"]), p(hout["qs"]), p(hout["ps"]), n, args.warmup,
+                          args.diag_every)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    swpic.swpic_step_host(sim.ctx, p(hin["Q"]), p(hin["P"]), p(hin["qs"]), p(hin["ps"]), p(hin["psi"]),
+                          p(hout["Q"]), p(hout["P"]), p(hout["qs"]), p(hout["ps"]), n, args.steps,
+                          args.diag_every)
+    dt = time.perf_counter() - t0
+    return {"value": n * args.steps / dt, "unit": UNIT,
+            "h2d_bytes_per_step": 20 * n / args.steps, "d2h_bytes_per_step": 16 * n / args.steps,
+            "note": "swpic_step_host: H2D of the 5 state arrays, field set-up, K steps, D2H of "
+                    "(Q, P, q*, p*), all inside the timed region"}
+
+
+def ensemble_leg(torch, swpic):
+    """256 independent Landau runs (uneven lattices 64^2..512^2, nx = side/2,
+    800 steps, diagnostics every step): one graph-captured batched context vs
+    the same runs one after another with plain launches.  Equal error: the
+    fitted damping rate of the linear runs (alpha < 0.05) against the kinetic
+    dispersion root."""
+    from workloads import physics as ph
+    runs = W.ensemble(precision=32)
+    steps = runs[0].steps
+
+    def run_batched():
+        sim = swpic.Simulation([(r.lattice.L, r.dt, r.nx, r.lattice.n) for r in runs], precision=32,
+                               diag_capacity=steps + 8)
+        for i, r in enumerate(runs):
+            sim.init_lattice(i, r.lattice)
+        swpic.swpic_refresh(sim.ctx)
+        swpic.swpic_synchronize(sim.ctx)
+        t0 = time.perf_counter()
+        sim.step(steps, 1)
+        swpic.swpic_synchronize(sim.ctx)
+        dt = time.perf_counter() - t0
+        diags = [sim.diagnostics(i) for i in range(len(runs))]
+        sim.close()
+        return dt, diags
+
+    def run_plain():
+        sims = []
+        for r in runs:
+            s = swpic.Simulation([(r.lattice.L, r.dt, r.nx, r.lattice.n)], precision=32,
+                                 use_graphs=False, diag_capacity=steps + 8, with_scratch=False)
+            s.init_lattice(0, r.lattice)
+            swpic.swpic_refresh(s.ctx)
+            sims.append(s)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for s in sims:
+            s.step(steps, 1)
+            swpic.swpic_synchronize(s.ctx)
+        dt = time.perf_counter() - t0
+        diags = [s.diagnostics() for s in sims]
+        for s in sims:
+            s.close()
+        return dt, diags
+
+    def gamma_err(diags):
+        errs = []
+        for r, d in zip(runs, diags):
+            if r.lattice.alpha >= 0.05:
+                continue
+            root = ph.landau_root(r.lattice.kx, 1.0 + 0.5 * r.lattice.kx - 0.1j)
+            try:
+                g, _, _ = ph.rate_fit(d[:, 0], d[:, 6], 2.0, 12.0, min_sep=1.2)
+            except ValueError:
+                continue
+            errs.append(abs(g / root.imag - 1))
+        return float(np.median(errs)) if errs else None, len(errs)
+
+    tb, db = run_batched()
+    tp, dp = run_plain()
+    eb, nb = gamma_err(db)
+    ep, _ = gamma_err(dp)
+    total = sum(r.lattice.n for r in runs)
+    return {"runs": len(runs), "particles": total, "steps": steps,
+            "batched_s": tb, "plain_s": tp, "speedup": tp / tb,
+            "batched_value": total * steps / tb, "plain_value": total * steps / tp,
+            "gamma_rel_err_median_batched": eb, "gamma_rel_err_median_plain": ep,
+            "runs_fitted": nb,
+            "note": "wall time of the step calls only; equal error = same median |gamma/gamma_root - 1|"}
+
+
+def cpu_baseline_leg(spec, args):
+    cols = 64                      # 64 x 4096 = 262,144 particles
+    k = 40
+    n, dt = time_oracle(spec, cols, k, 0, args.diag_every)
+    return {"value": n * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d of %d lattice columns (%d particles) of %s, %d steps, single-threaded "
+                      "plain-C FP64 oracle (includes its one-time dense LU of the Poisson matrix)" %
+                      (cols, spec.lattice.nq, n, spec.name, k)}
+
+
+if __name__ == "__main__":
+    main()

@@ -32,6 +32,8 @@ def lib():
         L.or_wrap.argtypes = [C.c_double, C.c_double]
         L.or_element.restype = C.c_int32
         L.or_element.argtypes = [C.c_double, C.c_double, C.c_int32]
+        L.or_element_f32.restype = C.c_int32
+        L.or_element_f32.argtypes = [C.c_double, C.c_double, C.c_int32]
         L.or_deposit.restype = None
         L.or_deposit.argtypes = [C.c_int64, _D, _D, _D, _I32, C.c_double, C.c_int32, _D]
         L.or_deposit_bruteforce.restype = None
@@ -54,7 +56,7 @@ def lib():
         L.or_run.restype = C.c_int
         L.or_run.argtypes = [C.c_int64, _D, _D, _D, _D, _D, C.c_int32, C.c_double,
                              C.c_double, C.c_int32, C.c_int32, C.c_int32, C.c_int32,
-                             _D, _I32, _D]
+                             _D, _I32, _D, C.c_int32]
         L.or_field_of_state.restype = C.c_int
         L.or_field_of_state.argtypes = [C.c_int64, _D, _D, _D, C.c_int32, C.c_double,
                                         C.c_int32, C.c_int32, _D, _D, _D, _D, _D]
@@ -217,10 +219,13 @@ def field_of_state(Q, p_star, psi_star, L, nx, d2_mode=D2_LUMPED, decorated=True
     return out
 
 
-def run(state, nx, L, dt, n_steps, diag_every=1, d2_mode=D2_LUMPED, decorated=True):
+def run(state, nx, L, dt, n_steps, diag_every=1, d2_mode=D2_LUMPED, decorated=True,
+        store_f32=False):
     """KDK leapfrog run (Sec. 5).  ``state`` is a dict with Q, P, qs, ps, psi
     (FP64 copies are made; the returned dict holds the final state, the
-    diagnostics history as an (n, 7) array and the final Phi)."""
+    diagnostics history as an (n, 7) array and the final Phi).  store_f32:
+    keep the state in FP32 storage (values rounded to FP32 after every update,
+    element decisions in FP32), arithmetic in FP64."""
     Q = np.array(state["Q"], dtype=np.float64)
     P = np.array(state["P"], dtype=np.float64)
     psi = np.array(state["psi"], dtype=np.float64)
@@ -233,7 +238,7 @@ def run(state, nx, L, dt, n_steps, diag_every=1, d2_mode=D2_LUMPED, decorated=Tr
     Phi = np.zeros(nx)
     rc = lib().or_run(n, _d(Q), _d(P), _d(qs), _d(ps), _d(psi), int(nx), float(L), float(dt),
                       int(d2_mode), int(bool(decorated)), int(n_steps), int(diag_every),
-                      _d(diag), C.byref(nd), _d(Phi))
+                      _d(diag), C.byref(nd), _d(Phi), int(bool(store_f32)))
     if rc != 0:
         raise RuntimeError("oracle run failed")
     return {"Q": Q, "P": P, "qs": qs, "ps": ps, "psi": psi,

@@ -58,6 +58,23 @@ int32_t or_element(double Q, double L, int32_t nx) {
     return i;
 }
 
+/* Element decided in FP32 from an FP32-stored position:
+ * floor(fl32(Q) * fl32(nx/L)), clamped.  Used when the state is kept in FP32
+ * storage, so the integer decision is taken in the storage precision. */
+int32_t or_element_f32(double Q, double L, int32_t nx) {
+    float q = (float)Q;
+    float inv_h = (float)((double)nx / L);
+    float prod = q * inv_h;
+    float s = floorf(prod);
+    int32_t i = (s != s) ? 0 : (int32_t)s;
+    if (i < 0) i = 0;
+    if (i > nx - 1) i = nx - 1;
+    return i;
+}
+
+/* Round a value to FP32 storage (and back to double). */
+static double to_f32(double x) { return (double)(float)x; }
+
 /* ------------------------------------------------------------------------ */
 /* Deposit: right-hand side assembly, Eq. (rhs-assembly) of Sec. 5           */
 /*   b_j = sum_a [ psi*_a phi_j(Q_a) - p*_a phi_j'(Q_a) ]                    */
@@ -387,22 +404,53 @@ void or_diagnostics(int64_t n, const double *P, const double *q_star,
 /* field, H, E_amp} is written at every step s with s % diag_every == 0      */
 /* (s = 0 .. n_steps); *n_diag receives the number of records written.       */
 /* decorated = 0 runs the point-particle PIC step (q*, p* ignored, may be    */
-/* NULL).  Returns 0 on success.                                             */
+/* NULL).  store_f32 = 1 keeps the state in FP32 storage: every updated      */
+/* value is rounded to FP32, element decisions are taken in FP32 from the    */
+/* stored positions, and the field tables are rounded to FP32; arithmetic    */
+/* stays FP64.  Returns 0 on success.                                        */
 /* ------------------------------------------------------------------------ */
 typedef struct {
-    int32_t nx, d2_mode, decorated;
+    int32_t nx, d2_mode, decorated, store_f32;
     double L;
     or_poisson *solver;
     double *b, *btilde, *Phi, *dphi, *d2, *dV, *d2V;
+    int32_t *elem;     /* FP32-storage element decisions (store_f32 only) */
 } or_field;
+
+static void decide_elements(or_field *f, int64_t n, const double *Q) {
+    for (int64_t a = 0; a < n; ++a) f->elem[a] = or_element_f32(Q[a], f->L, f->nx);
+}
 
 static int field_update(or_field *f, int64_t n, const double *Q, const double *p_star,
                         const double *psi_star) {
-    or_deposit(n, Q, f->decorated ? p_star : NULL, psi_star, NULL, f->L, f->nx, f->b);
+    if (f->store_f32) decide_elements(f, n, Q);
+    or_deposit(n, Q, f->decorated ? p_star : NULL, psi_star, f->store_f32 ? f->elem : NULL,
+               f->L, f->nx, f->b);
     double lambda = 0.0;
     or_poisson_solve(f->solver, f->b, f->Phi, &lambda);
     for (int32_t j = 0; j < f->nx; ++j) f->btilde[j] = f->b[j] - lambda;
-    return or_field_tables(f->nx, f->L, f->Phi, f->btilde, f->d2_mode, f->dphi, f->d2);
+    int rc = or_field_tables(f->nx, f->L, f->Phi, f->btilde, f->d2_mode, f->dphi, f->d2);
+    if (f->store_f32)
+        for (int32_t j = 0; j < f->nx; ++j) { f->dphi[j] = to_f32(f->dphi[j]); f->d2[j] = to_f32(f->d2[j]); }
+    return rc;
+}
+
+/* FP32 storage of the particle state after an update (store_f32 only); a
+ * position that rounds to L in FP32 wraps to 0. */
+static void store_state(const or_field *f, int64_t n, double *Q, double *P, double *qs, double *ps) {
+    if (!f->store_f32) return;
+    float Lf = (float)f->L;
+    for (int64_t a = 0; a < n; ++a) {
+        if (Q) {
+            float q = (float)Q[a];
+            if (q >= Lf) q -= Lf;
+            if (q < 0.0f) q += Lf;
+            Q[a] = (double)q;
+        }
+        P[a] = to_f32(P[a]);
+        if (qs) qs[a] = to_f32(qs[a]);
+        if (ps) ps[a] = to_f32(ps[a]);
+    }
 }
 
 static void write_diag(double *rec, double t, int64_t n, const double *P, const double *q_star,
@@ -416,10 +464,11 @@ static void write_diag(double *rec, double t, int64_t n, const double *P, const 
 int or_run(int64_t n, double *Q, double *P, double *q_star, double *p_star,
            const double *psi_star, int32_t nx, double L, double dt,
            int32_t d2_mode, int32_t decorated, int32_t n_steps, int32_t diag_every,
-           double *diag, int32_t *n_diag, double *Phi_out) {
+           double *diag, int32_t *n_diag, double *Phi_out, int32_t store_f32) {
     or_field f;
     memset(&f, 0, sizeof(f));
-    f.nx = nx; f.L = L; f.d2_mode = d2_mode; f.decorated = decorated;
+    f.nx = nx; f.L = L; f.d2_mode = d2_mode; f.decorated = decorated; f.store_f32 = store_f32;
+    f.elem = (int32_t *)calloc((size_t)(n > 0 ? n : 1), sizeof(int32_t));
     f.solver = or_poisson_new(nx, L);
     if (!f.solver) return -1;
     f.b = (double *)calloc((size_t)nx, sizeof(double));
@@ -435,13 +484,16 @@ int or_run(int64_t n, double *Q, double *P, double *q_star, double *p_star,
     int32_t nd = 0;
     if (rc == 0 && diag && diag_every > 0) write_diag(diag + 7 * (nd++), 0.0, n, P, qs, psi_star, &f);
     for (int32_t s = 1; rc == 0 && s <= n_steps; ++s) {
-        or_gather(n, Q, NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
+        or_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
         or_kick_values(n, ps, P, qs, f.dV, f.d2V, 0.5 * dt);
+        store_state(&f, n, NULL, P, qs, NULL);
         or_drift(n, Q, P, qs, ps, L, dt);
+        store_state(&f, n, Q, P, qs, ps);
         rc = field_update(&f, n, Q, ps, psi_star);
         if (rc != 0) break;
-        or_gather(n, Q, NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
+        or_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
         or_kick_values(n, ps, P, qs, f.dV, f.d2V, 0.5 * dt);
+        store_state(&f, n, NULL, P, qs, NULL);
         if (diag && diag_every > 0 && s % diag_every == 0)
             write_diag(diag + 7 * (nd++), (double)s * dt, n, P, qs, psi_star, &f);
     }
@@ -449,6 +501,7 @@ int or_run(int64_t n, double *Q, double *P, double *q_star, double *p_star,
     if (Phi_out) for (int32_t j = 0; j < nx; ++j) Phi_out[j] = f.Phi[j];
     or_poisson_free(f.solver);
     free(f.b); free(f.btilde); free(f.Phi); free(f.dphi); free(f.d2); free(f.dV); free(f.d2V);
+    free(f.elem);
     return rc;
 }
 

@@ -25,13 +25,6 @@ constexpr int64_t kSortChunk = 16384;
 constexpr int kFixedBits = 58;
 constexpr uint32_t PASS_NO_WRITE = 1u << 10;   // host-only marker (never sent to the device)
 
-struct Op {
-    int kind;          // 0 pass, 1 sort (into scratch), 2 event
-    double c1, c2, cd;
-    uint32_t flags;
-    bool from_scratch;
-};
-
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
@@ -445,52 +438,6 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
     return SWPIC_OK;
 }
 
-// Build the op list of n steps starting at ctx->step.
-std::vector<Op> build_ops(swpic_ctx *ctx, int n, int d) {
-    std::vector<Op> ops;
-    const int64_t s0 = ctx->step;
-    const bool can_sort = ctx->resort > 0 && ctx->scratch != nullptr && ctx->n_chunks > 0;
-    for (int i = 0; i <= n; ++i) {
-        const int64_t s = s0 + i;
-        bool sorted = false;
-        if (i < n && can_sort && s % ctx->resort == 0 && s > 0) {
-            ops.push_back(Op{1, 0, 0, 0, 0, false});
-            sorted = true;
-        }
-        Op p{0, 0, 0, 0, 0, sorted};
-        bool diag = d > 0 && s % d == 0;
-        if (i == 0) {
-            diag = diag && ctx->last_diag_step != s;
-            p.c1 = 0.0; p.c2 = 0.5; p.cd = 1.0;
-            p.flags = PASS_DEPOSIT | PASS_SOLVE | PASS_COUNT_STEP;
-        } else if (i < n) {
-            p.c1 = 0.5; p.c2 = 0.5; p.cd = 1.0;
-            p.flags = PASS_DEPOSIT | PASS_SOLVE | PASS_COUNT_STEP;
-        } else {
-            p.c1 = 0.5; p.c2 = 0.0; p.cd = 0.0;
-            p.flags = 0;
-        }
-        if (diag) p.flags |= PASS_DIAG;
-        ops.push_back(p);
-    }
-    return ops;
-}
-
-std::string ops_key(const swpic_ctx *ctx, const std::vector<Op> &ops) {
-    std::string k = std::to_string(ctx->tpb) + "/" + std::to_string(ctx->bpsm) + "/" +
-                    std::to_string(ctx->timing ? 1 : 0) + ":";
-    for (const Op &o : ops) {
-        k += o.kind == 1 ? 'S' : 'P';
-        if (o.kind == 0) {
-            char buf[48];
-            std::snprintf(buf, sizeof(buf), "%.2g,%.2g,%.2g,%x,%d;", o.c1, o.c2, o.cd, o.flags,
-                          o.from_scratch ? 1 : 0);
-            k += buf;
-        }
-    }
-    return k;
-}
-
 swpic_status ensure_events(swpic_ctx *ctx, size_t n) {
     while (ctx->events.size() < n) {
         cudaEvent_t e;
@@ -500,31 +447,55 @@ swpic_status ensure_events(swpic_ctx *ctx, size_t n) {
     return SWPIC_OK;
 }
 
-swpic_status enqueue_ops(swpic_ctx *ctx, const std::vector<Op> &ops, int64_t *kernels, int *passes) {
-    const int64_t l0 = ctx->launches;
-    int np = 0;
-    int npass = 0;
-    for (const Op &o : ops) if (o.kind == 0) ++npass;
-    if (ctx->timing) {
-        swpic_status s = ensure_events(ctx, 2 * (size_t)npass);
+// The pass that brings a call of n steps (starting at step s0) through integer time s.
+struct PassDesc {
+    double c1, c2, cd;
+    uint32_t flags;
+    bool sort_before;
+};
+
+bool can_sort(const swpic_ctx *ctx) {
+    return ctx->resort > 0 && ctx->scratch != nullptr && ctx->n_chunks > 0;
+}
+
+PassDesc pass_at(const swpic_ctx *ctx, int64_t s, int64_t s0, int64_t n, int d) {
+    PassDesc p{0, 0, 0, 0, false};
+    bool diag = d > 0 && s % d == 0;
+    if (s == s0) {                       // opening half-kick + drift + deposit + solve
+        diag = diag && ctx->last_diag_step != s;
+        p.c1 = 0.0; p.c2 = 0.5; p.cd = 1.0;
+        p.flags = PASS_DEPOSIT | PASS_SOLVE | PASS_COUNT_STEP;
+    } else if (s < s0 + n) {             // closing kick of step s, then the next step's opening
+        p.c1 = 0.5; p.c2 = 0.5; p.cd = 1.0;
+        p.flags = PASS_DEPOSIT | PASS_SOLVE | PASS_COUNT_STEP;
+    } else {                             // closing half-kick only
+        p.c1 = 0.5; p.c2 = 0.0; p.cd = 0.0;
+    }
+    if (diag) p.flags |= PASS_DIAG;
+    p.sort_before = s < s0 + n && s > 0 && can_sort(ctx) && s % ctx->resort == 0;
+    return p;
+}
+
+swpic_status enqueue_desc(swpic_ctx *ctx, const PassDesc &p, int *timed) {
+    if (p.sort_before) {
+        swpic_status s = enqueue_sort(ctx);
         if (s != SWPIC_OK) return s;
     }
-    for (const Op &o : ops) {
-        swpic_status s;
-        if (o.kind == 1) {
-            s = enqueue_sort(ctx);
-        } else {
-            if (ctx->timing) CK(cudaEventRecord(ctx->events[2 * np], ctx->stream));
-            s = enqueue_pass(ctx, o.c1, o.c2, o.cd, o.flags, o.from_scratch);
-            if (ctx->timing) CK(cudaEventRecord(ctx->events[2 * np + 1], ctx->stream));
-            ++np;
-        }
+    if (timed) {
+        swpic_status s = ensure_events(ctx, 2 * (size_t)(*timed + 1));
         if (s != SWPIC_OK) return s;
+        CK(cudaEventRecord(ctx->events[2 * (*timed)], ctx->stream));
     }
-    if (kernels) *kernels = ctx->launches - l0;
-    if (passes) *passes = np;
+    swpic_status s = enqueue_pass(ctx, p.c1, p.c2, p.cd, p.flags, p.sort_before);
+    if (s != SWPIC_OK) return s;
+    if (timed) {
+        CK(cudaEventRecord(ctx->events[2 * (*timed) + 1], ctx->stream));
+        ++*timed;
+    }
     return SWPIC_OK;
 }
+
+int64_t gcd64(int64_t a, int64_t b) { while (b) { int64_t t = a % b; a = b; b = t; } return a; }
 
 }  // namespace
 
@@ -727,49 +698,65 @@ swpic_status swpic_step(swpic_ctx *ctx, int32_t n_steps, int32_t diag_every) {
     if (s != SWPIC_OK) return s;
     if (n_steps < 0) return fail(ctx, SWPIC_EINVAL, "n_steps must be >= 0");
     if (n_steps == 0) return SWPIC_OK;
-    const std::vector<Op> ops = build_ops(ctx, n_steps, diag_every);
+    const int64_t s0 = ctx->step, n = n_steps;
+    const int d = diag_every > 0 ? diag_every : 0;
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(ctx->stream, &cap));
-    const bool use_graph = ctx->graphs && cap == cudaStreamCaptureStatusNone && ctx->stream != nullptr;
-    int npass = 0;
+    const bool use_graph = ctx->graphs && !ctx->timing && cap == cudaStreamCaptureStatusNone &&
+                           ctx->stream != nullptr;
+    int timed = 0;
+    int *tp = ctx->timing ? &timed : nullptr;
+    s = enqueue_desc(ctx, pass_at(ctx, s0, s0, n, d), tp);
+    if (s != SWPIC_OK) return s;
+    int64_t t = s0 + 1;
     if (use_graph) {
-        const std::string key = ops_key(ctx, ops);
-        auto it = ctx->graph_cache.find(key);
-        if (it == ctx->graph_cache.end()) {
-            if (ctx->graph_cache.size() >= 16) clear_graphs(ctx);
-            if (ctx->timing) { s = ensure_events(ctx, 2 * (size_t)(n_steps + 1)); if (s != SWPIC_OK) return s; }
-            CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-            GraphEntry ge;
-            const int64_t l0 = ctx->launches;
-            s = enqueue_ops(ctx, ops, &ge.kernels, &ge.n_passes);
-            ctx->launches = l0;
-            cudaGraph_t g = nullptr;
-            cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
-            if (s != SWPIC_OK) { if (g) cudaGraphDestroy(g); return s; }
-            if (e != cudaSuccess) return fail_cuda(ctx, "cudaStreamEndCapture", e);
-            e = cudaGraphInstantiate(&ge.exec, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return fail_cuda(ctx, "cudaGraphInstantiate", e);
-            it = ctx->graph_cache.emplace(key, ge).first;
+        // chunks of G full passes; their pattern (diagnostics, sorts) repeats with `period`
+        const int64_t a = d > 0 ? d : 1, b = can_sort(ctx) ? ctx->resort : 1;
+        const int64_t period = a / gcd64(a, b) * b;
+        const int64_t G = period >= 64 ? period : period * ((64 + period - 1) / period);
+        while (t + G <= s0 + n && G <= 4096) {
+            char key[160];
+            std::snprintf(key, sizeof(key), "G%lld/p%lld/d%d/r%d/t%d/b%d", (long long)G,
+                          (long long)(t % period), d, can_sort(ctx) ? ctx->resort : 0, ctx->tpb,
+                          ctx->bpsm);
+            auto it = ctx->graph_cache.find(key);
+            if (it == ctx->graph_cache.end()) {
+                if (ctx->graph_cache.size() >= 32) clear_graphs(ctx);
+                GraphEntry ge;
+                const int64_t l0 = ctx->launches;
+                CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+                swpic_status q = SWPIC_OK;
+                for (int64_t k = 0; k < G && q == SWPIC_OK; ++k)
+                    q = enqueue_desc(ctx, pass_at(ctx, t + k, s0, n, d), nullptr);
+                cudaGraph_t g = nullptr;
+                cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+                ge.kernels = ctx->launches - l0;
+                ge.n_passes = (int)G;
+                ctx->launches = l0;
+                if (q != SWPIC_OK) { if (g) cudaGraphDestroy(g); return q; }
+                if (e != cudaSuccess) return fail_cuda(ctx, "cudaStreamEndCapture", e);
+                e = cudaGraphInstantiate(&ge.exec, g, 0);
+                cudaGraphDestroy(g);
+                if (e != cudaSuccess) return fail_cuda(ctx, "cudaGraphInstantiate", e);
+                it = ctx->graph_cache.emplace(key, ge).first;
+            }
+            CK(cudaGraphLaunch(it->second.exec, ctx->stream));
+            ctx->launches += it->second.kernels;
+            t += G;
         }
-        CK(cudaGraphLaunch(it->second.exec, ctx->stream));
-        ctx->launches += it->second.kernels;
-        npass = it->second.n_passes;
-    } else {
-        s = enqueue_ops(ctx, ops, nullptr, &npass);
+    }
+    for (; t < s0 + n; ++t) {
+        s = enqueue_desc(ctx, pass_at(ctx, t, s0, n, d), tp);
         if (s != SWPIC_OK) return s;
     }
-    ctx->n_timed = ctx->timing ? npass : 0;
-    // the last record written is at the highest diag step of this call
-    {
-        int64_t st = ctx->step;
-        for (const Op &o : ops) {
-            if (o.kind != 0) continue;
-            if (o.flags & PASS_DIAG) ctx->last_diag_step = st;
-            if (o.flags & PASS_COUNT_STEP) ++st;
-        }
+    s = enqueue_desc(ctx, pass_at(ctx, s0 + n, s0, n, d), tp);
+    if (s != SWPIC_OK) return s;
+    ctx->n_timed = timed;
+    if (d > 0) {
+        const int64_t last = (s0 + n) / d * d;      // newest record of this call
+        if (last >= s0) ctx->last_diag_step = last;
     }
-    ctx->step += n_steps;
+    ctx->step = s0 + n;
     return SWPIC_OK;
 }
 

@@ -13,13 +13,15 @@
 // c1 = c2 = 1/2, cd = 1: the two half-kicks with the same field are applied
 // one after the other, so the pass is bit-for-bit the kick-drift-kick step.
 //
-// Deposit: every thread accumulates the contributions of its consecutive
-// particles while they stay in one element (sorted particles give long runs)
-// and flushes a run into the CTA's shared-memory mesh on an element change.
-// ATOMIC mode flushes float/double shared atomics; DETERMINISTIC mode flushes
-// 64-bit fixed-point integer atomics, which are associative, so the result
-// does not depend on the order in which threads flush.  At the end of its
-// particle range a CTA adds its mesh into the run's global int64 accumulator.
+// Deposit: each thread handles 16-byte vectors of consecutive particles.  When
+// every lane of a warp finds all particles of its vector in one element, the
+// lane first sums them; then lanes with equal elements in consecutive lanes are
+// combined by a segmented shuffle reduction and one lane per segment adds the
+// sum to the CTA's shared-memory mesh.  ATOMIC mode uses float/double shared
+// atomics; DETERMINISTIC mode converts the (fixed-order) warp sums to 64-bit
+// fixed point and uses integer atomics, which are associative, so the result
+// does not depend on thread scheduling.  At the end of its particle range a
+// CTA adds its mesh into the run's global int64 accumulator.
 //
 // The CTA that completes the last particles of a run (a completion counter,
 // no spinning) then removes the mean of b (Eq. neutrality / zero-mean test
@@ -217,36 +219,54 @@ struct Kahan {
     }
 };
 
-template <typename T, bool DEC, int MODE>
+template <typename T>
 struct Thread {
-    using T2 = typename Vec2<T>::type;
-    // deposit run
-    int cur;
-    T a0, a1;
-    // diagnostics
-    Kahan<T> mom, kin;
+    Kahan<T> mom, kin;     // diagnostics partials (integer-time P, q*)
 };
 
 template <typename T, int MODE>
-__device__ __forceinline__ void flush_run(int cur, T a0, T a1, void *mesh, double scale, int32_t *err) {
-    if (cur < 0) return;
+__device__ __forceinline__ void mesh_add(int key, T a0, T a1, void *mesh, double scale, int32_t *err) {
     if (MODE == SWPIC_DEPOSIT_ATOMIC) {
         T *m = reinterpret_cast<T *>(mesh);
-        atomicAdd(m + cur, a0);
-        atomicAdd(m + cur + 1, a1);
+        atomicAdd(m + key, a0);
+        atomicAdd(m + key + 1, a1);
     } else {
         unsigned long long *m = reinterpret_cast<unsigned long long *>(mesh);
-        atomicAdd(m + cur, to_fixed(a0, scale, err));
-        atomicAdd(m + cur + 1, to_fixed(a1, scale, err));
+        atomicAdd(m + key, to_fixed(a0, scale, err));
+        atomicAdd(m + key + 1, to_fixed(a1, scale, err));
     }
 }
 
-template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
+// Warp-aggregated deposit: lanes holding the same element in consecutive lanes
+// form a segment; a segmented suffix sum (5 shuffle steps, fixed order) gives
+// the segment's first lane the segment total, and only that lane touches the
+// shared mesh.  key < 0 marks an empty slot.  All 32 lanes must call this.
+template <typename T, int MODE>
+__device__ __forceinline__ void warp_deposit(int key, T a0, T a1, void *mesh, double scale,
+                                             int32_t *err) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(full, key, 1);
+    const bool head = (lane == 0) || (prev != key);
+    const unsigned heads = __ballot_sync(full, head);
+    const unsigned above = (lane == 31) ? 0u : (heads & (0xffffffffu << (lane + 1)));
+    const int seg_end = above ? (__ffs(above) - 2) : 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const T b0 = __shfl_down_sync(full, a0, off);
+        const T b1 = __shfl_down_sync(full, a1, off);
+        if (lane + off <= seg_end) { a0 += b0; a1 += b1; }
+    }
+    if (head && key >= 0) mesh_add<T, MODE>(key, a0, a1, mesh, scale, err);
+}
+
+// Push one particle; returns its deposit (element of the drifted Q, weights of
+// nodes key and key+1) in key/w0/w1 when DEP.
+template <typename T, bool DEC, bool DEP, bool DIAG, int D2>
 __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
                                          const typename Vec2<T>::type *tab, const int nx,
                                          const Geo<T> &G, const T k1, const T k2, const T kd,
-                                         Thread<T, DEC, MODE> &th, void *mesh, double scale,
-                                         int32_t *err) {
+                                         Thread<T> &th, int &key, T &w0, T &w1) {
     const int i = elem_of(Q, G.inv_h, nx);
     const auto f = tab[i];
     T d2 = T(0);
@@ -273,22 +293,14 @@ __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
     Q = wrap_pos(Q + kd * P, G.L);
     if (DEC) ps = ps - kd * qs;
     if (DEP) {
-        const int i2 = elem_of(Q, G.inv_h, nx);
-        const T xi = Q * G.inv_h - (T)i2;
-        T w0 = w * (T(1) - xi), w1 = w * xi;
+        key = elem_of(Q, G.inv_h, nx);
+        const T xi = Q * G.inv_h - (T)key;
+        w0 = w * (T(1) - xi);
+        w1 = w * xi;
         if (DEC) {
             const T dq = ps * G.inv_h;
             w0 += dq;
             w1 -= dq;
-        }
-        if (i2 == th.cur) {
-            th.a0 += w0;
-            th.a1 += w1;
-        } else {
-            flush_run<T, MODE>(th.cur, th.a0, th.a1, mesh, scale, err);
-            th.cur = i2;
-            th.a0 = w0;
-            th.a1 = w1;
         }
     }
 }
@@ -304,8 +316,7 @@ __device__ __forceinline__ int find_run(const RunDev *runs, int n_runs, int64_t 
 
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
 __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, int64_t e,
-                                const typename Vec2<T>::type *s_tab, void *s_mesh,
-                                Thread<T, DEC, MODE> &th) {
+                                const typename Vec2<T>::type *s_tab, void *s_mesh, Thread<T> &th) {
     using V = typename Vec16<T>::type;
     constexpr int VW = Vec16<T>::n;
     const Geo<T> G = geo_of(R, T());
@@ -320,15 +331,19 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
     T *qso = reinterpret_cast<T *>(a.qso), *pso = reinterpret_cast<T *>(a.pso);
     T *wo = reinterpret_cast<T *>(a.wo);
 
+    // unaligned head / tail (fewer than VW particles each): one particle per
+    // thread, shared-memory atomics without aggregation
     auto scalar = [&](int64_t k) {
         T Q = Qi[k], P = Pi[k], w = wi[k];
         T qs = DEC ? qsi[k] : T(0), ps = DEC ? psi[k] : T(0);
-        push_one<T, DEC, MODE, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, th, s_mesh,
-                                              scale, a.err);
+        int key = -1;
+        T w0 = T(0), w1 = T(0);
+        push_one<T, DEC, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, th, key, w0, w1);
         Qo[k] = Q;
         Po[k] = P;
         if (DEC) { qso[k] = qs; pso[k] = ps; }
         if (wpsi) wo[k] = w;
+        if (DEP) mesh_add<T, MODE>(key, w0, w1, s_mesh, scale, a.err);
     };
 
     const int64_t vs = (s + VW - 1) / VW * VW;
@@ -341,60 +356,68 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
     const int64_t v0 = vs / VW, v1 = ve / VW;
     constexpr int U = 2;
     const int64_t stride = (int64_t)blockDim.x;
-    int64_t v = v0 + threadIdx.x;
-    for (; v + (U - 1) * stride < v1; v += U * stride) {
+    // warp-uniform trip count: every lane runs every iteration; out-of-range
+    // lanes carry empty deposit slots
+    for (int64_t vb = v0; vb < v1; vb += U * stride) {
         V q[U], p[U], x[U], y[U], m[U];
+        bool ok[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t vv = v + u * stride;
-            q[u] = reinterpret_cast<const V *>(Qi)[vv];
-            p[u] = reinterpret_cast<const V *>(Pi)[vv];
-            m[u] = reinterpret_cast<const V *>(wi)[vv];
-            if (DEC) {
-                x[u] = reinterpret_cast<const V *>(qsi)[vv];
-                y[u] = reinterpret_cast<const V *>(psi)[vv];
+            const int64_t vv = vb + u * stride + threadIdx.x;
+            ok[u] = vv < v1;
+            if (ok[u]) {
+                q[u] = reinterpret_cast<const V *>(Qi)[vv];
+                p[u] = reinterpret_cast<const V *>(Pi)[vv];
+                m[u] = reinterpret_cast<const V *>(wi)[vv];
+                if (DEC) {
+                    x[u] = reinterpret_cast<const V *>(qsi)[vv];
+                    y[u] = reinterpret_cast<const V *>(psi)[vv];
+                }
             }
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            T *Q = reinterpret_cast<T *>(&q[u]), *P = reinterpret_cast<T *>(&p[u]);
-            T *X = reinterpret_cast<T *>(&x[u]), *Y = reinterpret_cast<T *>(&y[u]);
-            const T *M = reinterpret_cast<const T *>(&m[u]);
+            int key[VW];
+            T w0[VW], w1[VW];
+            if (ok[u]) {
+                T *Q = reinterpret_cast<T *>(&q[u]), *P = reinterpret_cast<T *>(&p[u]);
+                T *X = reinterpret_cast<T *>(&x[u]), *Y = reinterpret_cast<T *>(&y[u]);
+                const T *M = reinterpret_cast<const T *>(&m[u]);
 #pragma unroll
-            for (int l = 0; l < VW; ++l) {
-                T qs = DEC ? X[l] : T(0), ps = DEC ? Y[l] : T(0);
-                push_one<T, DEC, MODE, DEP, DIAG, D2>(Q[l], P[l], qs, ps, M[l], s_tab, nx, G, k1, k2,
-                                                      kd, th, s_mesh, scale, a.err);
-                if (DEC) { X[l] = qs; Y[l] = ps; }
-            }
-            const int64_t vv = v + u * stride;
-            reinterpret_cast<V *>(Qo)[vv] = q[u];
-            reinterpret_cast<V *>(Po)[vv] = p[u];
-            if (DEC) {
-                reinterpret_cast<V *>(qso)[vv] = x[u];
-                reinterpret_cast<V *>(pso)[vv] = y[u];
-            }
-            if (wpsi) reinterpret_cast<V *>(wo)[vv] = m[u];
-        }
-    }
-    for (; v < v1; v += stride) {
-        V q = reinterpret_cast<const V *>(Qi)[v], p = reinterpret_cast<const V *>(Pi)[v];
-        V m = reinterpret_cast<const V *>(wi)[v], x, y;
-        if (DEC) { x = reinterpret_cast<const V *>(qsi)[v]; y = reinterpret_cast<const V *>(psi)[v]; }
-        T *Q = reinterpret_cast<T *>(&q), *P = reinterpret_cast<T *>(&p);
-        T *X = reinterpret_cast<T *>(&x), *Y = reinterpret_cast<T *>(&y);
-        const T *M = reinterpret_cast<const T *>(&m);
+                for (int l = 0; l < VW; ++l) {
+                    T qs = DEC ? X[l] : T(0), ps = DEC ? Y[l] : T(0);
+                    push_one<T, DEC, DEP, DIAG, D2>(Q[l], P[l], qs, ps, M[l], s_tab, nx, G, k1, k2,
+                                                    kd, th, key[l], w0[l], w1[l]);
+                    if (DEC) { X[l] = qs; Y[l] = ps; }
+                }
+                const int64_t vv = vb + u * stride + threadIdx.x;
+                reinterpret_cast<V *>(Qo)[vv] = q[u];
+                reinterpret_cast<V *>(Po)[vv] = p[u];
+                if (DEC) {
+                    reinterpret_cast<V *>(qso)[vv] = x[u];
+                    reinterpret_cast<V *>(pso)[vv] = y[u];
+                }
+                if (wpsi) reinterpret_cast<V *>(wo)[vv] = m[u];
+            } else {
 #pragma unroll
-        for (int l = 0; l < VW; ++l) {
-            T qs = DEC ? X[l] : T(0), ps = DEC ? Y[l] : T(0);
-            push_one<T, DEC, MODE, DEP, DIAG, D2>(Q[l], P[l], qs, ps, M[l], s_tab, nx, G, k1, k2, kd,
-                                                  th, s_mesh, scale, a.err);
-            if (DEC) { X[l] = qs; Y[l] = ps; }
+                for (int l = 0; l < VW; ++l) { key[l] = -1; w0[l] = T(0); w1[l] = T(0); }
+            }
+            if (DEP) {
+                bool one = true;
+#pragma unroll
+                for (int l = 1; l < VW; ++l) one = one && (key[l] == key[0]);
+                if (__all_sync(0xffffffffu, one)) {
+                    T s0 = w0[0], s1 = w1[0];
+#pragma unroll
+                    for (int l = 1; l < VW; ++l) { s0 += w0[l]; s1 += w1[l]; }
+                    warp_deposit<T, MODE>(key[0], s0, s1, s_mesh, scale, a.err);
+                } else {
+#pragma unroll
+                    for (int l = 0; l < VW; ++l)
+                        warp_deposit<T, MODE>(key[l], w0[l], w1[l], s_mesh, scale, a.err);
+                }
+            }
         }
-        reinterpret_cast<V *>(Qo)[v] = q;
-        reinterpret_cast<V *>(Po)[v] = p;
-        if (DEC) { reinterpret_cast<V *>(qso)[v] = x; reinterpret_cast<V *>(pso)[v] = y; }
-        if (wpsi) reinterpret_cast<V *>(wo)[v] = m;
     }
     for (int64_t k = ve + threadIdx.x; k < e; k += blockDim.x) scalar(k);
 }
@@ -429,7 +452,7 @@ __device__ void finish_run(const PassArgs &a, const RunDev &R, int r, unsigned c
 }
 
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
-__global__ void __launch_bounds__(1024) k_pass(PassArgs a) {
+__global__ void __launch_bounds__(512) k_pass(PassArgs a) {
     using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_last;
@@ -460,13 +483,10 @@ __global__ void __launch_bounds__(1024) k_pass(PassArgs a) {
             }
         }
         __syncthreads();
-        Thread<T, DEC, MODE> th;
-        th.cur = -1;
-        th.a0 = th.a1 = T(0);
+        Thread<T> th;
         th.mom = {T(0), T(0)};
         th.kin = {T(0), T(0)};
         process_segment<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, th);
-        if (DEP) flush_run<T, MODE>(th.cur, th.a0, th.a1, s_mesh, R.fx_scale, a.err);
         __syncthreads();
         if (DEP) {
             unsigned long long *gacc = a.acc + R.mesh_off;

@@ -174,7 +174,7 @@ def test_solve_matches_thm1_single_particle():
     the closed form (Eq. solution) for the monopole and the explicit P1
     dipole solution (proof of Thm 2), up to the gauge constant."""
     need_gpu()
-    import physics as ph
+    from workloads import physics as ph
     from paper_2605_21794_gb300 import swpic
     L, nx, Q, psi, ps = 5.0, 40, 1.2345, 0.8, 0.0
     sim = _sim([(L, 0.1, nx, 1)], 64)

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-import physics as ph
+from workloads import physics as ph
 import workloads as W
 
 
@@ -501,3 +501,20 @@ def test_momentum_and_kinetic_are_pairings_with_the_ansatz():
         kin += np.sum(0.5 * p * p * fp) * dp - 0.5 * st["psi"][a] * s * s
     assert abs(d["momentum"] - mom) < 1e-10 * max(1.0, abs(mom))
     assert abs(d["kinetic"] - kin) < 1e-9 * max(1.0, abs(kin))
+
+
+def test_fp32_storage_mode_rounds_state_and_decides_in_fp32():
+    """store_f32 keeps every updated value representable in FP32 and takes the
+    element decision from the stored FP32 position; it stays within FP32
+    rounding of the FP64 run."""
+    spec = W.landau_linear(jitter=1e-3)
+    jx, jv = W.jitter(spec.lattice)
+    st = O.init_lattice(spec.lattice, jx, jv)
+    st = {k: v.astype(np.float32).astype(np.float64) for k, v in st.items()}
+    L = spec.lattice.L
+    a = O.run(st, spec.nx, L, spec.dt, 10, diag_every=0, store_f32=True)
+    b = O.run(st, spec.nx, L, spec.dt, 10, diag_every=0)
+    for k in ("Q", "P", "qs", "ps"):
+        assert np.array_equal(a[k].astype(np.float32).astype(np.float64), a[k]), k
+        assert np.abs(a[k] - b[k]).max() <= 1e-5 * max(np.abs(b[k]).max(), 1e-30), k
+    assert np.all((a["Q"] >= 0) & (a["Q"] < L))
