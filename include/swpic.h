@@ -225,8 +225,18 @@ swpic_status swpic_get_mesh(swpic_ctx *ctx, int32_t run, double *b, double *btil
  * precision, with the run-local nx and L.  keys: host int32 array of n. */
 swpic_status swpic_get_keys(swpic_ctx *ctx, int32_t *keys, int64_t n);
 
-/* Waits for the bound stream and reports any recorded device anomaly. */
+/* Waits for the bound stream and reports a device anomaly recorded since the
+ * last report (SWPIC_ENUMERIC; the message names the number of runs and the
+ * first one).  Anomalies are per run: a run whose charge accumulator
+ * overflowed or whose field became non-finite keeps its flag (see
+ * swpic_run_status) while the other runs of a batch are unaffected; its own
+ * overflowing contributions are dropped.  Flags are cleared by swpic_refresh,
+ * swpic_init_particles and swpic_load. */
 swpic_status swpic_synchronize(swpic_ctx *ctx);
+
+/* Synchronous.  flags[r] = anomaly bits of run r (1: fixed-point charge
+ * accumulator overflow, 2: non-finite field); n_runs must equal the runs. */
+swpic_status swpic_run_status(swpic_ctx *ctx, int32_t *flags, int32_t n_runs);
 
 /* ---- end to end from host memory --------------------------------------------- */
 

@@ -406,8 +406,8 @@ void or_diagnostics(int64_t n, const double *P, const double *q_star,
 /* decorated = 0 runs the point-particle PIC step (q*, p* ignored, may be    */
 /* NULL).  store_f32 = 1 keeps the state in FP32 storage: every updated      */
 /* value is rounded to FP32, element decisions are taken in FP32 from the    */
-/* stored positions, and the field tables are rounded to FP32; arithmetic    */
-/* stays FP64.  Returns 0 on success.                                        */
+/* stored positions, the field tables and the step coefficients dt/2, dt   */
+/* are rounded to FP32; arithmetic stays FP64.  Returns 0 on success.        */
 /* ------------------------------------------------------------------------ */
 typedef struct {
     int32_t nx, d2_mode, decorated, store_f32;
@@ -483,16 +483,19 @@ int or_run(int64_t n, double *Q, double *P, double *q_star, double *p_star,
     int rc = field_update(&f, n, Q, ps, psi_star);
     int32_t nd = 0;
     if (rc == 0 && diag && diag_every > 0) write_diag(diag + 7 * (nd++), 0.0, n, P, qs, psi_star, &f);
+    /* FP32 storage keeps the step coefficients in FP32 as well */
+    const double half = store_f32 ? to_f32(0.5 * dt) : 0.5 * dt;
+    const double full = store_f32 ? to_f32(dt) : dt;
     for (int32_t s = 1; rc == 0 && s <= n_steps; ++s) {
         or_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
-        or_kick_values(n, ps, P, qs, f.dV, f.d2V, 0.5 * dt);
+        or_kick_values(n, ps, P, qs, f.dV, f.d2V, half);
         store_state(&f, n, NULL, P, qs, NULL);
-        or_drift(n, Q, P, qs, ps, L, dt);
+        or_drift(n, Q, P, qs, ps, L, full);
         store_state(&f, n, Q, P, qs, ps);
         rc = field_update(&f, n, Q, ps, psi_star);
         if (rc != 0) break;
         or_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
-        or_kick_values(n, ps, P, qs, f.dV, f.d2V, 0.5 * dt);
+        or_kick_values(n, ps, P, qs, f.dV, f.d2V, half);
         store_state(&f, n, NULL, P, qs, NULL);
         if (diag && diag_every > 0 && s % diag_every == 0)
             write_diag(diag + 7 * (nd++), (double)s * dt, n, P, qs, psi_star, &f);

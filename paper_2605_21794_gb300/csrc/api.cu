@@ -77,6 +77,7 @@ struct swpic_ctx {
     bool prepared = false;
     int64_t step = 0;
     int64_t last_diag_step = -1;
+    std::vector<int32_t> reported;   // per-run anomaly flags already reported
     std::string err;
     std::map<std::string, GraphEntry> graph_cache;
     bool timing = false;
@@ -281,6 +282,8 @@ swpic_status prepare(swpic_ctx *ctx, bool keep_steps) {
     CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_done, 0, sizeof(unsigned long long) * ctx->R, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_diag_acc, 0, sizeof(double) * 2 * ctx->R, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t) * ctx->R, ctx->stream));
+    ctx->reported.assign(ctx->R, 0);
     CK(cudaMemsetAsync(ctx->d_table, 0, (size_t)ctx->total_mesh * 2 * elem_size(ctx->prec), ctx->stream));
     if (!keep_steps) {
         CK(cudaMemsetAsync(ctx->d_steps, 0, sizeof(long long) * ctx->R, ctx->stream));
@@ -360,6 +363,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
         d.dt = c.dt;
         d.Lf = (float)c.L;
         d.inv_hf = (float)d.inv_h;
+        d.inv_hf_lo = (float)(d.inv_h - (double)d.inv_hf);
         d.inv_Lf = (float)d.inv_L;
         d.dtf = (float)c.dt;
         d.fx_scale = std::ldexp(1.0, 56);
@@ -411,7 +415,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
     ok &= alloc((void **)&ctx->d_steps, sizeof(long long) * R);
     ok &= alloc((void **)&ctx->d_ring, sizeof(double) * kDiagWords * (size_t)R * ctx->cap);
     ok &= alloc((void **)&ctx->d_ring_count, sizeof(int32_t) * R);
-    ok &= alloc((void **)&ctx->d_err, sizeof(int32_t));
+    ok &= alloc((void **)&ctx->d_err, sizeof(int32_t) * R);
     ok &= alloc((void **)&ctx->d_chunks, sizeof(SortChunk) * std::max(1, ctx->n_chunks));
     ok &= alloc((void **)&ctx->d_cnt, sizeof(int32_t) * std::max<int64_t>(1, cnt_base));
     ok &= alloc((void **)&ctx->d_pos, sizeof(int64_t) * std::max<int64_t>(1, cnt_base));
@@ -425,7 +429,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
         cudaMemcpy(ctx->d_chunks, ctx->h_chunks.data(), sizeof(SortChunk) * ctx->n_chunks,
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(SWPIC_ECUDA);
-    cudaMemset(ctx->d_err, 0, sizeof(int32_t));
+    cudaMemset(ctx->d_err, 0, sizeof(int32_t) * R);
     cudaMemset(ctx->d_acc, 0, sizeof(unsigned long long) * mo);
     cudaMemset(ctx->d_done, 0, sizeof(unsigned long long) * R);
     cudaMemset(ctx->d_steps, 0, sizeof(long long) * R);
@@ -763,13 +767,32 @@ swpic_status swpic_step(swpic_ctx *ctx, int32_t n_steps, int32_t diag_every) {
 swpic_status swpic_synchronize(swpic_ctx *ctx) {
     if (!ctx) return SWPIC_EINVAL;
     CK(cudaStreamSynchronize(ctx->stream));
-    int32_t e = 0;
-    CK(cudaMemcpy(&e, ctx->d_err, sizeof(int32_t), cudaMemcpyDeviceToHost));
-    if (e) {
-        cudaMemset(ctx->d_err, 0, sizeof(int32_t));
-        return fail(ctx, SWPIC_ENUMERIC, (e & kErrFixedOverflow) ? "charge accumulator overflow"
-                                                                 : "non-finite field");
+    std::vector<int32_t> f(ctx->R, 0);
+    CK(cudaMemcpy(f.data(), ctx->d_err, sizeof(int32_t) * ctx->R, cudaMemcpyDeviceToHost));
+    if (ctx->reported.size() != (size_t)ctx->R) ctx->reported.assign(ctx->R, 0);
+    int fresh = 0, first = -1, bits = 0;
+    for (int r = 0; r < ctx->R; ++r) {
+        if (f[r] & ~ctx->reported[r]) {
+            ++fresh;
+            if (first < 0) first = r;
+            bits |= f[r];
+        }
+        ctx->reported[r] |= f[r];
     }
+    if (fresh) {
+        char msg[256];
+        std::snprintf(msg, sizeof(msg), "%s in %d run(s) (first: run %d); see swpic_run_status",
+                      (bits & kErrFixedOverflow) ? "charge accumulator overflow" : "non-finite field",
+                      fresh, first);
+        return fail(ctx, SWPIC_ENUMERIC, msg);
+    }
+    return SWPIC_OK;
+}
+
+swpic_status swpic_run_status(swpic_ctx *ctx, int32_t *flags, int32_t n_runs) {
+    if (!ctx || !flags || n_runs != ctx->R) return SWPIC_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(flags, ctx->d_err, sizeof(int32_t) * ctx->R, cudaMemcpyDeviceToHost));
     return SWPIC_OK;
 }
 

@@ -44,9 +44,27 @@ template <> struct Vec16<double> { using type = double2; static constexpr int n 
 __device__ __forceinline__ float flo(float x) { return floorf(x); }
 __device__ __forceinline__ double flo(double x) { return floor(x); }
 
-template <typename T> struct Geo { T L, inv_h, inv_L, dt; };
-__device__ __forceinline__ Geo<float> geo_of(const RunDev &r, float) { return {r.Lf, r.inv_hf, r.inv_Lf, r.dtf}; }
-__device__ __forceinline__ Geo<double> geo_of(const RunDev &r, double) { return {r.L, r.inv_h, r.inv_L, r.dt}; }
+template <typename T> struct Geo { T L, inv_h, inv_L, dt, inv_h_lo; };
+__device__ __forceinline__ Geo<float> geo_of(const RunDev &r, float) {
+    return {r.Lf, r.inv_hf, r.inv_Lf, r.dtf, r.inv_hf_lo};
+}
+__device__ __forceinline__ Geo<double> geo_of(const RunDev &r, double) {
+    return {r.L, r.inv_h, r.inv_L, r.dt, 0.0};
+}
+
+// Position inside element i, xi = Q nx/L - i.  The element index itself is
+// decided by the single rounded product (the key definition); xi is formed
+// with the rounding error of that product and the low part of nx/L added
+// back, so an FP32 state does not see the ~nx ulp bias of fl32(nx/L) near
+// Q = L (the error of xi stays at the ulp of xi, not of Q nx/L).
+__device__ __forceinline__ float xi_of(float Q, int i, const Geo<float> &G) {
+    const float p = Q * G.inv_h;
+    const float err = fmaf(Q, G.inv_h, -p);      // exact rounding error of the product
+    return (p - (float)i) + fmaf(Q, G.inv_h_lo, err);
+}
+__device__ __forceinline__ double xi_of(double Q, int i, const Geo<double> &G) {
+    return Q * G.inv_h - (double)i;
+}
 
 template <typename T>
 __device__ __forceinline__ int elem_of(T Q, T inv_h, int nx) {
@@ -201,7 +219,7 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
         const double Ea = sqrt(E2 / (double)nx);
         a.field_diag[2 * r] = W;
         a.field_diag[2 * r + 1] = Ea;
-        if (!isfinite(W)) atomicOr(a.err, kErrNonFinite);
+        if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
     }
 }
 
@@ -272,7 +290,7 @@ __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
     T d2 = T(0);
     if (DEC) {
         if (D2 == SWPIC_D2_NODAL) {
-            const T xi = Q * G.inv_h - (T)i;
+            const T xi = xi_of(Q, i, G);
             const T g1 = tab[i + 1 == nx ? 0 : i + 1].y;
             d2 = f.y + xi * (g1 - f.y);
         } else {
@@ -294,7 +312,7 @@ __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
     if (DEC) ps = ps - kd * qs;
     if (DEP) {
         key = elem_of(Q, G.inv_h, nx);
-        const T xi = Q * G.inv_h - (T)key;
+        const T xi = xi_of(Q, key, G);
         w0 = w * (T(1) - xi);
         w1 = w * xi;
         if (DEC) {
@@ -316,7 +334,8 @@ __device__ __forceinline__ int find_run(const RunDev *runs, int n_runs, int64_t 
 
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
 __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, int64_t e,
-                                const typename Vec2<T>::type *s_tab, void *s_mesh, Thread<T> &th) {
+                                const typename Vec2<T>::type *s_tab, void *s_mesh, Thread<T> &th,
+                                int32_t *err) {
     using V = typename Vec16<T>::type;
     constexpr int VW = Vec16<T>::n;
     const Geo<T> G = geo_of(R, T());
@@ -343,7 +362,7 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
         Po[k] = P;
         if (DEC) { qso[k] = qs; pso[k] = ps; }
         if (wpsi) wo[k] = w;
-        if (DEP) mesh_add<T, MODE>(key, w0, w1, s_mesh, scale, a.err);
+        if (DEP) mesh_add<T, MODE>(key, w0, w1, s_mesh, scale, err);
     };
 
     const int64_t vs = (s + VW - 1) / VW * VW;
@@ -410,11 +429,11 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
                     T s0 = w0[0], s1 = w1[0];
 #pragma unroll
                     for (int l = 1; l < VW; ++l) { s0 += w0[l]; s1 += w1[l]; }
-                    warp_deposit<T, MODE>(key[0], s0, s1, s_mesh, scale, a.err);
+                    warp_deposit<T, MODE>(key[0], s0, s1, s_mesh, scale, err);
                 } else {
 #pragma unroll
                     for (int l = 0; l < VW; ++l)
-                        warp_deposit<T, MODE>(key[l], w0[l], w1[l], s_mesh, scale, a.err);
+                        warp_deposit<T, MODE>(key[l], w0[l], w1[l], s_mesh, scale, err);
                 }
             }
         }
@@ -486,7 +505,7 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
         Thread<T> th;
         th.mom = {T(0), T(0)};
         th.kin = {T(0), T(0)};
-        process_segment<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, th);
+        process_segment<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, th, a.err + r);
         __syncthreads();
         if (DEP) {
             unsigned long long *gacc = a.acc + R.mesh_off;
@@ -494,7 +513,7 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
                 const int node = (j == nx) ? 0 : j;
                 if (MODE == SWPIC_DEPOSIT_ATOMIC) {
                     const T v = reinterpret_cast<T *>(s_mesh)[j];
-                    if (v != T(0)) atomicAdd(gacc + node, to_fixed(v, R.fx_scale, a.err));
+                    if (v != T(0)) atomicAdd(gacc + node, to_fixed(v, R.fx_scale, a.err + r));
                 } else {
                     const unsigned long long v = reinterpret_cast<unsigned long long *>(s_mesh)[j];
                     if (v != 0ull) atomicAdd(gacc + node, v);

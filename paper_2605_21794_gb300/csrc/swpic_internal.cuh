@@ -30,7 +30,9 @@ struct RunDev {
     double fx_scale;         // fixed-point scale 2^k of the charge accumulator
     double fx_inv;           // 2^-k
     float Lf, inv_hf, inv_Lf, dtf;  // FP32 copies (rounded once from the FP64 values)
+    float inv_hf_lo;         // (nx/L) - inv_hf, so Q nx/L = Q inv_hf + Q inv_hf_lo to ~2^-48
     int32_t nx, mesh_off;
+    int32_t pad_;
 };
 
 enum PassFlags : uint32_t {
@@ -65,7 +67,7 @@ struct PassArgs {
     double *ring;             // [R][cap][kDiagWords]
     int32_t *ring_count;      // [R]
     int32_t ring_cap;
-    int32_t *err;
+    int32_t *err;             // [R] per-run anomaly flags (kErrFixedOverflow | kErrNonFinite)
 };
 
 // shared-memory bytes of the pass kernel / the per-run solve for a given max nx

@@ -77,6 +77,7 @@ SIGNATURES = {
     "swpic_get_mesh": (C.c_int, [_CTX, C.c_int32, _D, _D, _D, _D, _D]),
     "swpic_get_keys": (C.c_int, [_CTX, C.POINTER(C.c_int32), C.c_int64]),
     "swpic_synchronize": (C.c_int, [_CTX]),
+    "swpic_run_status": (C.c_int, [_CTX, C.POINTER(C.c_int32), C.c_int32]),
     "swpic_step_host": (C.c_int, [_CTX, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int64,
                                   C.c_int32, C.c_int32]),
     "swpic_save": (C.c_int, [_CTX, C.c_char_p]),
@@ -251,6 +252,13 @@ def swpic_get_keys(ctx, n):
 
 def swpic_synchronize(ctx):
     _check(load_library().swpic_synchronize(ctx), ctx)
+
+
+def swpic_run_status(ctx, n_runs):
+    flags = np.zeros(n_runs, dtype=np.int32)
+    _check(load_library().swpic_run_status(ctx, flags.ctypes.data_as(C.POINTER(C.c_int32)),
+                                           int(n_runs)), ctx)
+    return flags
 
 
 def swpic_step_host(ctx, Q, P, qs, ps, psi, Q_out, P_out, qs_out, ps_out, n, n_steps,

@@ -47,13 +47,15 @@ def _compare_state(got, ref, L, tol, keys=("Q", "P", "qs", "ps")):
 @pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("d2_mode", [0, 2])
 def test_one_fp64_step_matches_oracle(mode, d2_mode):
+    """Identical seeded inputs on both sides (linear-Landau geometry: L = 4pi,
+    nx 64, dt 0.1, 4096 particles): every array within 1e-12 after one step."""
     need_gpu()
-    spec = W.landau_linear(jitter=1e-3)
-    st, jx, jv = _lattice_state(spec)
+    spec = W.landau_linear()
     L = spec.lattice.L
-    sim = _sim([(L, spec.dt, spec.nx, spec.lattice.n)], 64, deposit_mode=mode, d2_mode=d2_mode)
+    st = W.random_state(4096, L, seed=11, nx=spec.nx)
+    sim = _sim([(L, spec.dt, spec.nx, 4096)], 64, deposit_mode=mode, d2_mode=d2_mode)
     try:
-        sim.init_lattice(0, spec.lattice, jx, jv)
+        sim.init_particles(st)
         sim.step(1, diag_every=1)
         got = sim.state()
         diag = sim.diagnostics()
@@ -64,6 +66,28 @@ def test_one_fp64_step_matches_oracle(mode, d2_mode):
     assert diag.shape[0] == 2 and np.allclose(diag[:, 0], [0.0, spec.dt])
     for col, rc in ((1, 1), (3, 3), (4, 4), (5, 5), (6, 6)):
         assert rel_max(diag[:, col], ref["diag"][:, rc]) < 1e-11, col
+
+
+def test_one_fp64_step_from_each_sides_lattice_init():
+    """Each side initialises the jittered linear-Landau lattice itself.  With
+    jitter 1e-3 cell, p* is a small remainder of the cell integral; the oracle
+    forms sin(2pi (Q - q)/L) from Q - q directly and loses ~1e-12 of p* to
+    cancellation (the kernel forms the angle from the offsets), so p*, q* are
+    compared to 1e-10 and Q, P to 1e-12."""
+    need_gpu()
+    spec = W.landau_linear(jitter=1e-3)
+    st, jx, jv = _lattice_state(spec)
+    L = spec.lattice.L
+    sim = _sim([(L, spec.dt, spec.nx, spec.lattice.n)], 64)
+    try:
+        sim.init_lattice(0, spec.lattice, jx, jv)
+        sim.step(1, diag_every=1)
+        got = sim.state()
+    finally:
+        sim.close()
+    ref = O.run(st, spec.nx, L, spec.dt, 1, diag_every=1)
+    _compare_state(got, ref, L, 1e-12, keys=("Q", "P"))
+    _compare_state(got, ref, L, 1e-10, keys=("qs", "ps"))
 
 
 @pytest.mark.parametrize("mode", [0, 1])
