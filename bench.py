@@ -381,11 +381,12 @@ def ensemble_leg(torch, swpic):
         swpic.swpic_synchronize(sim.ctx)
         t0 = time.perf_counter()
         sim.step(steps, 1)
-        swpic.swpic_synchronize(sim.ctx)
+        sync_tolerant(sim.ctx)
         dt = time.perf_counter() - t0
+        flags = swpic.swpic_run_status(sim.ctx, len(runs))
         diags = [sim.diagnostics(i) for i in range(len(runs))]
         sim.close()
-        return dt, diags
+        return dt, diags, flags
 
     def run_plain():
         sims = []
@@ -399,12 +400,22 @@ def ensemble_leg(torch, swpic):
         t0 = time.perf_counter()
         for s in sims:
             s.step(steps, 1)
-            swpic.swpic_synchronize(s.ctx)
+            sync_tolerant(s.ctx)
         dt = time.perf_counter() - t0
+        flags = np.array([swpic.swpic_run_status(s.ctx, 1)[0] for s in sims])
         diags = [s.diagnostics() for s in sims]
         for s in sims:
             s.close()
-        return dt, diags
+        return dt, diags, flags
+
+    def sync_tolerant(ctx):
+        # runs whose decorations blow up (nonlinear runs late in time) flag a
+        # fixed-point overflow; they are counted, the others are unaffected
+        try:
+            swpic.swpic_synchronize(ctx)
+        except swpic.SwpicError as e:
+            if e.status != swpic.SWPIC_ENUMERIC:
+                raise
 
     def gamma_err(diags):
         errs = []
@@ -419,8 +430,8 @@ def ensemble_leg(torch, swpic):
             errs.append(abs(g / root.imag - 1))
         return float(np.median(errs)) if errs else None, len(errs)
 
-    tb, db = run_batched()
-    tp, dp = run_plain()
+    tb, db, fb = run_batched()
+    tp, dp, fp = run_plain()
     eb, nb = gamma_err(db)
     ep, _ = gamma_err(dp)
     total = sum(r.lattice.n for r in runs)
@@ -429,6 +440,8 @@ def ensemble_leg(torch, swpic):
             "batched_value": total * steps / tb, "plain_value": total * steps / tp,
             "gamma_rel_err_median_batched": eb, "gamma_rel_err_median_plain": ep,
             "runs_fitted": nb,
+            "runs_flagged_batched": int(np.count_nonzero(fb)),
+            "runs_flagged_plain": int(np.count_nonzero(fp)),
             "note": "wall time of the step calls only; equal error = same median |gamma/gamma_root - 1|"}
 
 

@@ -51,6 +51,7 @@ struct swpic_ctx {
     RunDev *d_runs = nullptr;
     std::vector<RunDev> h_runs;
     unsigned long long *d_acc = nullptr, *d_done = nullptr;
+    long long *d_snap = nullptr;
     void *d_table = nullptr;
     double *d_b = nullptr, *d_bt = nullptr, *d_e = nullptr, *d_phi = nullptr;
     double *d_diag_acc = nullptr, *d_field_diag = nullptr, *d_mass = nullptr, *d_mabs = nullptr;
@@ -155,7 +156,7 @@ void free_all(swpic_ctx *ctx) {
     ctx->graph_cache.clear();
     for (auto ev : ctx->events) cudaEventDestroy(ev);
     ctx->events.clear();
-    void *ptrs[] = {ctx->d_runs, ctx->d_acc, ctx->d_done, ctx->d_table, ctx->d_b, ctx->d_bt, ctx->d_e,
+    void *ptrs[] = {ctx->d_runs, ctx->d_acc, ctx->d_snap, ctx->d_done, ctx->d_table, ctx->d_b, ctx->d_bt, ctx->d_e,
                     ctx->d_phi, ctx->d_diag_acc, ctx->d_field_diag, ctx->d_mass, ctx->d_mabs,
                     ctx->d_steps, ctx->d_ring, ctx->d_ring_count, ctx->d_err, ctx->d_chunks,
                     ctx->d_cnt, ctx->d_pos, ctx->d_scan_tmp, ctx->d_partials};
@@ -179,6 +180,7 @@ PassArgs base_args(swpic_ctx *ctx) {
     a.max_nx = ctx->max_nx;
     a.runs = ctx->d_runs;
     a.acc = ctx->d_acc;
+    a.snap = ctx->d_snap;
     a.table = ctx->d_table;
     a.b = ctx->d_b; a.btilde = ctx->d_bt; a.efield = ctx->d_e;
     a.run_done = ctx->d_done;
@@ -402,6 +404,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
     bool ok = true;
     ok &= alloc((void **)&ctx->d_runs, sizeof(RunDev) * R);
     ok &= alloc((void **)&ctx->d_acc, sizeof(unsigned long long) * mo);
+    ok &= alloc((void **)&ctx->d_snap, sizeof(long long) * mo);
     ok &= alloc((void **)&ctx->d_done, sizeof(unsigned long long) * R);
     ok &= alloc(&ctx->d_table, (size_t)mo * 2 * es);
     ok &= alloc((void **)&ctx->d_b, sizeof(double) * mo);
@@ -431,6 +434,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
         return bail(SWPIC_ECUDA);
     cudaMemset(ctx->d_err, 0, sizeof(int32_t) * R);
     cudaMemset(ctx->d_acc, 0, sizeof(unsigned long long) * mo);
+    cudaMemset(ctx->d_snap, 0, sizeof(long long) * mo);
     cudaMemset(ctx->d_done, 0, sizeof(unsigned long long) * R);
     cudaMemset(ctx->d_steps, 0, sizeof(long long) * R);
     cudaMemset(ctx->d_ring_count, 0, sizeof(int32_t) * R);
@@ -829,6 +833,12 @@ swpic_status swpic_get_mesh(swpic_ctx *ctx, int32_t run, double *b, double *btil
     swpic_status s = ensure_prepared(ctx);
     if (s != SWPIC_OK) return s;
     const int nx = ctx->nx[run], mo = ctx->mesh_off[run];
+    {
+        PassArgs b = base_args(ctx);
+        b.flags = PASS_READOUT;
+        CK(launch_solve_runs(ctx->prec, b, 256, solve_smem_bytes(ctx->max_nx), ctx->stream));
+        ctx->launches += 1;
+    }
     if (Phi) {
         CK(launch_phi(ctx->d_runs, ctx->R, ctx->d_e, ctx->d_phi, ctx->max_nx, ctx->stream));
         ctx->launches += 1;

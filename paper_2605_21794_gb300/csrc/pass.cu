@@ -145,8 +145,19 @@ __device__ long long block_exscan_ll(long long v, long long *sh) {
 }
 
 // ---------------------------------------------------------------------------
-// per-run field solve by one CTA (FP64, exact integer neutralisation)
-// full = false: only b and btilde are written and acc is left as is.
+// per-run field solve by one CTA.
+//
+// The charge arrives as int64 fixed point (acc_j = b_j 2^k).  Neutralisation
+// and Gauss's law are exact in integers:
+//   S = sum_j acc_j = q nx + rem (0 <= rem < nx),  bt_j = acc_j - q
+//   e_int_j = sum_{i<=j} bt_i                       (exact prefix)
+// so btilde_j = (bt_j - rem/nx) 2^-k and the element field, after the
+// zero-sum gauge, is e_j = (e_int_j - mean(e_int)) 2^-k - (j + 1 - (nx+1)/2) rem/nx 2^-k.
+// The table takes phi_h' = -e_j and the lumped phi'' (e_{j-1} - e_{j+1})/(2h)
+// = -(bt_j + bt_{j+1}) 2^-k/(2h) straight from the integers (FP32 path: one
+// rounding to float; FP64 path: FP64).  The accumulator is snapshot for
+// read-out and zeroed for the next pass; W = (h/2) sum e^2 and E_amp are kept
+// in FP64.  full = false: only the snapshot (swpic_deposit's read-out).
 // ---------------------------------------------------------------------------
 template <typename T>
 __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned char *smem, bool full) {
@@ -154,64 +165,71 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
     __shared__ long long sh_ll[32];
     __shared__ double sh_d[32];
     const int nx = R.nx, tid = threadIdx.x, nt = blockDim.x;
-    long long *s_acc = reinterpret_cast<long long *>(smem);
-    double *s_e = reinterpret_cast<double *>(smem + (size_t)a.max_nx * 8);
+    long long *s_v = reinterpret_cast<long long *>(smem);      // acc, then e_int
     const int per = (nx + nt - 1) / nt;
     const int j0 = min(nx, tid * per), j1 = min(nx, j0 + per);
     unsigned long long *acc = a.acc + R.mesh_off;
+    long long *snap = a.snap + R.mesh_off;
     const int off = R.mesh_off;
 
     long long loc = 0;
     for (int j = j0; j < j1; ++j) {
-        long long v = (long long)__ldcg(acc + j);
-        s_acc[j] = v;
+        const long long v = (long long)__ldcg(acc + j);
+        s_v[j] = v;
+        snap[j] = v;
         loc += v;
-    }
-    const long long S = block_sum_ll(loc, sh_ll);          // exact (mod 2^64)
-    long long q = S / nx, rem = S % nx;                    // S = q nx + rem, 0 <= rem < nx
-    if (rem < 0) { rem += nx; q -= 1; }
-    const double inv = R.fx_inv;
-    const double rem_node = (double)rem * inv / (double)nx;   // fractional mean per node
-
-    long long tot = 0;
-    for (int j = j0; j < j1; ++j) tot += s_acc[j] - q;
-    long long p = block_exscan_ll(tot, sh_ll);
-    double esum = 0.0;
-    for (int j = j0; j < j1; ++j) {
-        const long long bt = s_acc[j] - q;
-        p += bt;                                           // exact prefix of btilde
-        const double btd = (double)bt * inv - rem_node;
-        a.b[off + j] = (double)s_acc[j] * inv;
-        a.btilde[off + j] = btd;
-        const double er = (double)p * inv - (double)(j + 1) * rem_node;
-        s_e[j] = er;
-        esum += er;
+        if (full) acc[j] = 0ull;
     }
     if (!full) return;
-    const double mean_e = block_sum_d(esum, sh_d) / (double)nx;
-    for (int j = j0; j < j1; ++j) s_e[j] -= mean_e;
-    __syncthreads();
+    const long long S = block_sum_ll(loc, sh_ll);            // exact (mod 2^64)
+    long long q = S / nx, rem = S % nx;
+    if (rem < 0) { rem += nx; q -= 1; }
+    long long tot = 0;
+    for (int j = j0; j < j1; ++j) tot += s_v[j] - q;
+    long long p = block_exscan_ll(tot, sh_ll);
+    double es = 0.0;
+    for (int j = j0; j < j1; ++j) {
+        p += s_v[j] - q;
+        s_v[j] = p;                                          // e_int_j (own range)
+        es += (double)p;
+    }
+    const double mean = block_sum_d(es, sh_d) / (double)nx;   // syncs: all e_int visible
+    const long long mean_i = (long long)floor(mean);
+    const double mfrac = mean - (double)mean_i;
+    const double inv = R.fx_inv;
+    const double rem_node = (double)rem * inv / (double)nx;
+    const double cen = 0.5 * (double)(nx + 1);
     T2 *tab = reinterpret_cast<T2 *>(a.table) + off;
     double e2 = 0.0;
-    const double half_inv_h = 0.5 * R.inv_h;
     for (int j = j0; j < j1; ++j) {
-        const double ej = s_e[j];
-        e2 += ej * ej;
-        a.efield[off + j] = ej;
-        double d2;
-        if (a.d2_mode == SWPIC_D2_NODAL) {
-            const long long bt = s_acc[j] - q;
-            d2 = -((double)bt * inv - rem_node) * R.inv_h;
-        } else {
-            const double em = s_e[j == 0 ? nx - 1 : j - 1];
-            const double ep = s_e[j == nx - 1 ? 0 : j + 1];
-            d2 = (em - ep) * half_inv_h;
-        }
+        const int jm = (j == 0) ? nx - 1 : j - 1, jp = (j == nx - 1) ? 0 : j + 1;
+        const long long ei = s_v[j] - mean_i;
+        const long long btj = (j == 0) ? s_v[0] : s_v[j] - s_v[j - 1];
         T2 t;
-        t.x = (T)(-ej);
-        t.y = (T)d2;
+        if (sizeof(T) == 4) {
+            // FP32 table straight from the exact integers; the sub-quantum
+            // gauge/remainder terms (< nx quanta) are below FP32 resolution
+            const float finv = (float)inv;                   // power of two: exact
+            const float ef = (float)ei * finv;
+            t.x = (T)(-ef);
+            if (a.d2_mode == SWPIC_D2_NODAL)
+                t.y = (T)(-(float)btj * finv * (float)R.inv_h);
+            else
+                t.y = (T)((float)(s_v[jm] - s_v[jp]) * finv * (float)(0.5 * R.inv_h));
+            e2 += (double)ef * (double)ef;
+        } else {
+            auto efield = [&](int k) {
+                return ((double)(s_v[k] - mean_i) - mfrac) * inv - ((double)(k + 1) - cen) * rem_node;
+            };
+            const double ej = efield(j);
+            t.x = (T)(-ej);
+            if (a.d2_mode == SWPIC_D2_NODAL)
+                t.y = (T)(-((double)btj * inv - rem_node) * R.inv_h);
+            else
+                t.y = (T)((efield(jm) - efield(jp)) * (0.5 * R.inv_h));
+            e2 += ej * ej;
+        }
         tab[j] = t;
-        acc[j] = 0ull;
     }
     const double E2 = block_sum_d(e2, sh_d);
     if (tid == 0) {
@@ -221,6 +239,41 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
         a.field_diag[2 * r + 1] = Ea;
         if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
     }
+}
+
+// FP64 read-out of a run's mesh quantities from the integer snapshot (one CTA
+// per run): b, btilde, E (zero-sum gauge) exactly as the solve defines them.
+__device__ void readout_run(const PassArgs &a, const RunDev &R, unsigned char *smem) {
+    __shared__ long long sh_ll[32];
+    __shared__ double sh_d[32];
+    const int nx = R.nx, tid = threadIdx.x, nt = blockDim.x;
+    long long *s_v = reinterpret_cast<long long *>(smem);
+    const int per = (nx + nt - 1) / nt;
+    const int j0 = min(nx, tid * per), j1 = min(nx, j0 + per);
+    const long long *snap = a.snap + R.mesh_off;
+    const int off = R.mesh_off;
+    long long loc = 0;
+    for (int j = j0; j < j1; ++j) { s_v[j] = snap[j]; loc += s_v[j]; }
+    const long long S = block_sum_ll(loc, sh_ll);
+    long long q = S / nx, rem = S % nx;
+    if (rem < 0) { rem += nx; q -= 1; }
+    const double inv = R.fx_inv;
+    const double rem_node = (double)rem * inv / (double)nx;
+    long long tot = 0;
+    for (int j = j0; j < j1; ++j) tot += s_v[j] - q;
+    long long p = block_exscan_ll(tot, sh_ll);
+    double es = 0.0;
+    for (int j = j0; j < j1; ++j) {
+        const long long bt = s_v[j] - q;
+        p += bt;
+        a.b[off + j] = (double)s_v[j] * inv;
+        a.btilde[off + j] = (double)bt * inv - rem_node;
+        const double er = (double)p * inv - (double)(j + 1) * rem_node;
+        a.efield[off + j] = er;
+        es += er;
+    }
+    const double mean_e = block_sum_d(es, sh_d) / (double)nx;
+    for (int j = j0; j < j1; ++j) a.efield[off + j] -= mean_e;
 }
 
 // ---------------------------------------------------------------------------
@@ -561,7 +614,8 @@ __global__ void __launch_bounds__(1024) k_solve_runs(PassArgs a, int full) {
     const int r = blockIdx.x;
     if (r >= a.n_runs) return;
     const RunDev R = a.runs[r];
-    solve_run<T>(a, R, r, smem, full != 0);
+    if (full == 2) readout_run(a, R, smem);
+    else solve_run<T>(a, R, r, smem, full != 0);
 }
 
 // Phi from e: Phi_{j+1} = Phi_j - h e_j, then zero mean (one CTA per run)
@@ -600,7 +654,7 @@ __global__ void __launch_bounds__(1024) k_phi(const RunDev *runs, int n_runs, co
 }
 
 // ---------------------------------------------------------------------------
-size_t solve_smem_bytes(int max_nx) { return (size_t)max_nx * 16; }
+size_t solve_smem_bytes(int max_nx) { return (size_t)max_nx * 8; }
 
 size_t pass_smem_bytes(int prec, int max_nx, int mode) {
     const size_t t2 = (prec == SWPIC_F64) ? 16 : 8;
@@ -656,7 +710,8 @@ cudaError_t launch_pass(int prec, bool decorated, int mode, const PassArgs &a, i
 }
 
 cudaError_t launch_solve_runs(int prec, const PassArgs &a, int tpb, size_t smem, cudaStream_t s) {
-    const int full = (a.flags & PASS_SOLVE) ? 1 : 0;
+    // PASS_SOLVE: full solve; PASS_READOUT: FP64 read-out from the snapshot; else snapshot only
+    const int full = (a.flags & PASS_READOUT) ? 2 : ((a.flags & PASS_SOLVE) ? 1 : 0);
     if (prec == SWPIC_F64) {
         cudaError_t err = cudaFuncSetAttribute(k_solve_runs<double>,
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

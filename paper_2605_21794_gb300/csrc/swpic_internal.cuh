@@ -41,7 +41,7 @@ enum PassFlags : uint32_t {
     PASS_DIAG = 4u,        // accumulate integer-time (P, q*) sums, last CTA writes a record
     PASS_WRITE_PSI = 8u,   // write psi* to the output arrays (input came from the sort buffer)
     PASS_COUNT_STEP = 16u, // last CTA advances the run's step counter
-    PASS_ZERO_ONLY = 32u,  // (internal) nothing to push: only the last-CTA work
+    PASS_READOUT = 32u,    // (solve kernel only) FP64 b, btilde, E from the snapshot
 };
 
 struct PassArgs {
@@ -57,6 +57,7 @@ struct PassArgs {
     double c1, c2, cd;        // closing kick, opening kick, drift: fractions of dt
     uint32_t flags;
     unsigned long long *acc;  // int64 bit patterns
+    long long *snap;          // int64 snapshot of acc taken by the last solve (read-out)
     void *table;              // T2 per element
     double *b, *btilde, *efield;
     unsigned long long *run_done;
