@@ -435,16 +435,16 @@ static int field_update(or_field *f, int64_t n, const double *Q, const double *p
     return rc;
 }
 
-/* FP32 storage of the particle state after an update (store_f32 only); a
- * position that rounds to L in FP32 wraps to 0. */
+/* FP32 storage of the particle state after an update (store_f32 only).  The
+ * domain stays [0, L) with the exact L: a position whose FP32 rounding lands
+ * on or beyond L is wrapped by L (in FP64) and rounded again. */
 static void store_state(const or_field *f, int64_t n, double *Q, double *P, double *qs, double *ps) {
     if (!f->store_f32) return;
-    float Lf = (float)f->L;
     for (int64_t a = 0; a < n; ++a) {
         if (Q) {
             float q = (float)Q[a];
-            if (q >= Lf) q -= Lf;
-            if (q < 0.0f) q += Lf;
+            if ((double)q >= f->L) q = (float)((double)q - f->L);
+            if (q < 0.0f) q = (float)((double)q + f->L);
             Q[a] = (double)q;
         }
         P[a] = to_f32(P[a]);

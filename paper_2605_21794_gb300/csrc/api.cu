@@ -366,6 +366,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
         d.Lf = (float)c.L;
         d.inv_hf = (float)d.inv_h;
         d.inv_hf_lo = (float)(d.inv_h - (double)d.inv_hf);
+        d.L_lo = (float)(c.L - (double)d.Lf);
         d.inv_Lf = (float)d.inv_L;
         d.dtf = (float)c.dt;
         d.fx_scale = std::ldexp(1.0, 56);

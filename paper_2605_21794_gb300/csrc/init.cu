@@ -71,7 +71,7 @@ __global__ void k_init_lattice(T *Q, T *P, T *qs, T *ps, T *psi, int64_t p0, dou
         const double Pa = vc + ov * dv;
         const double w = Xc[i] * Vc[j] * dx * dv;
         T Qt = (T)Qa;
-        if (Qt >= (T)L) Qt = T(0);
+        if ((double)Qt >= L) Qt = (T)((double)Qt - L);   // rounded onto/over L: wrap exactly
         const int64_t o = p0 + a;
         Q[o] = Qt;
         P[o] = (T)Pa;

@@ -44,12 +44,12 @@ template <> struct Vec16<double> { using type = double2; static constexpr int n 
 __device__ __forceinline__ float flo(float x) { return floorf(x); }
 __device__ __forceinline__ double flo(double x) { return floor(x); }
 
-template <typename T> struct Geo { T L, inv_h, inv_L, dt, inv_h_lo; };
+template <typename T> struct Geo { T L, inv_h, inv_L, dt, inv_h_lo, L_lo; };
 __device__ __forceinline__ Geo<float> geo_of(const RunDev &r, float) {
-    return {r.Lf, r.inv_hf, r.inv_Lf, r.dtf, r.inv_hf_lo};
+    return {r.Lf, r.inv_hf, r.inv_Lf, r.dtf, r.inv_hf_lo, r.L_lo};
 }
 __device__ __forceinline__ Geo<double> geo_of(const RunDev &r, double) {
-    return {r.L, r.inv_h, r.inv_L, r.dt, 0.0};
+    return {r.L, r.inv_h, r.inv_L, r.dt, 0.0, 0.0};
 }
 
 // Position inside element i, xi = Q nx/L - i.  The element index itself is
@@ -82,6 +82,35 @@ __device__ __forceinline__ T wrap_pos(T Q, T L) {
         if (Q < T(0)) Q += L;
     }
     return Q;
+}
+
+// Drift with the periodic wrap, Q' = Q + kd P mod L.
+// FP64: the domain length is the double L itself.
+__device__ __forceinline__ double drift_wrap(double Q, double P, double kd, const Geo<double> &G) {
+    return wrap_pos(Q + kd * P, G.L);
+}
+// FP32: L is not a float; it is carried as L = L_hi + L_lo (L_hi = fl32(L)).
+// Inside-test and shifts use both parts, and a crossing of L is formed from
+// the unrounded sum, Q' = (Q - L_hi) + kd P - L_lo, so particles that wrap
+// are not displaced by L - fl32(L) (which would bias the charge at the
+// periodic node).  A value that can only round onto L moves to the wrapped
+// side, as the FP32 rounding of the exact position does.
+__device__ __forceinline__ bool inside_f32(float Q, const Geo<float> &G) {
+    return Q >= 0.0f && (Q - G.L) < G.L_lo;        // Q - L_hi is exact near L
+}
+__device__ __forceinline__ float drift_wrap(float Q, float P, float kd, const Geo<float> &G) {
+    float Qn = fmaf(kd, P, Q);
+    if (inside_f32(Qn, G) || Qn != Qn) return Qn;
+    if (Qn >= 0.0f) Qn = fmaf(kd, P, Q - G.L) - G.L_lo;   // crossed L
+    else Qn = (Qn + G.L) + G.L_lo;                          // crossed 0
+    if (inside_f32(Qn, G)) return Qn;
+    // several periods in one step, or a value that rounded onto the boundary
+    const float k = floorf(Qn * G.inv_L);
+    Qn = fmaf(-k, G.L_lo, fmaf(-k, G.L, Qn));
+    if (Qn >= 0.0f && !inside_f32(Qn, G)) Qn = (Qn - G.L) - G.L_lo;
+    if (Qn < 0.0f) Qn = (Qn + G.L) + G.L_lo;
+    if (!inside_f32(Qn, G)) Qn = (Qn < 0.0f) ? 0.0f : (Qn - G.L) - G.L_lo;
+    return Qn < 0.0f ? 0.0f : Qn;
 }
 
 // value * 2^k as an int64 bit pattern; out-of-range (or NaN) sets the error flag
@@ -159,67 +188,105 @@ __device__ long long block_exscan_ll(long long v, long long *sh) {
 // read-out and zeroed for the next pass; W = (h/2) sum e^2 and E_amp are kept
 // in FP64.  full = false: only the snapshot (swpic_deposit's read-out).
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ __int128 warp_sum_i128(__int128 v) {
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long lo = (unsigned long long)v, hi = (unsigned long long)(v >> 64);
+        const unsigned long long olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        const unsigned long long ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        v += (__int128)(((unsigned __int128)ohi << 64) | (unsigned __int128)olo);
+    }
+    return v;
+}
+
+// shared-memory index of mesh entry j, padded by one word per 32 so that the
+// contiguous per-lane chunks of the serial part do not all hit one bank
+__device__ __forceinline__ int pad_idx(int j) { return j + (j >> 5); }
+
 template <typename T>
 __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned char *smem, bool full) {
     using T2 = typename Vec2<T>::type;
-    __shared__ long long sh_ll[32];
-    __shared__ double sh_d[32];
+    __shared__ long long s_par[4];                 // q, rem, mean_i, (spare)
+    __shared__ double s_mfrac;
+    __shared__ __int128 s_e2[32];
     const int nx = R.nx, tid = threadIdx.x, nt = blockDim.x;
-    long long *s_v = reinterpret_cast<long long *>(smem);      // acc, then e_int
-    const int per = (nx + nt - 1) / nt;
-    const int j0 = min(nx, tid * per), j1 = min(nx, j0 + per);
+    const int lane = tid & 31, warp = tid >> 5;
+    long long *s_v = reinterpret_cast<long long *>(smem);      // acc, then e_int (padded)
     unsigned long long *acc = a.acc + R.mesh_off;
     long long *snap = a.snap + R.mesh_off;
     const int off = R.mesh_off;
 
-    long long loc = 0;
-    for (int j = j0; j < j1; ++j) {
+    // 1. all threads: stage acc (coalesced), snapshot it, clear it
+    for (int j = tid; j < nx; j += nt) {
         const long long v = (long long)__ldcg(acc + j);
-        s_v[j] = v;
+        s_v[pad_idx(j)] = v;
         snap[j] = v;
-        loc += v;
         if (full) acc[j] = 0ull;
     }
     if (!full) return;
-    const long long S = block_sum_ll(loc, sh_ll);            // exact (mod 2^64)
-    long long q = S / nx, rem = S % nx;
-    if (rem < 0) { rem += nx; q -= 1; }
-    long long tot = 0;
-    for (int j = j0; j < j1; ++j) tot += s_v[j] - q;
-    long long p = block_exscan_ll(tot, sh_ll);
-    double es = 0.0;
-    for (int j = j0; j < j1; ++j) {
-        p += s_v[j] - q;
-        s_v[j] = p;                                          // e_int_j (own range)
-        es += (double)p;
+    __syncthreads();
+    // 2. warp 0: exact integer neutralisation, Gauss prefix and its mean
+    if (warp == 0) {
+        const int per = (nx + 31) >> 5;
+        const int j0 = min(nx, lane * per), j1 = min(nx, j0 + per);
+        long long loc = 0;
+        for (int j = j0; j < j1; ++j) loc += s_v[pad_idx(j)];
+        const long long S = warp_sum_ll(loc);
+        long long q = S / nx, rem = S % nx;
+        if (rem < 0) { rem += nx; q -= 1; }
+        long long tot = 0;
+        for (int j = j0; j < j1; ++j) tot += s_v[pad_idx(j)] - q;
+        long long inc = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        long long p = inc - tot;
+        __int128 es = 0;
+        for (int j = j0; j < j1; ++j) {
+            p += s_v[pad_idx(j)] - q;
+            s_v[pad_idx(j)] = p;                    // e_int_j
+            es += (__int128)p;
+        }
+        es = warp_sum_i128(es);
+        if (lane == 0) {
+            const double mean = (double)es / (double)nx;
+            const long long mean_i = (long long)floor(mean);
+            s_par[0] = q;
+            s_par[1] = rem;
+            s_par[2] = mean_i;
+            s_mfrac = ((double)(es - (__int128)mean_i * nx)) / (double)nx;
+        }
     }
-    const double mean = block_sum_d(es, sh_d) / (double)nx;   // syncs: all e_int visible
-    const long long mean_i = (long long)floor(mean);
-    const double mfrac = mean - (double)mean_i;
+    __syncthreads();
+    // 3. all threads: table, sum of E^2
+    const long long rem = s_par[1], mean_i = s_par[2];
+    const double mfrac = s_mfrac;
     const double inv = R.fx_inv;
     const double rem_node = (double)rem * inv / (double)nx;
     const double cen = 0.5 * (double)(nx + 1);
     T2 *tab = reinterpret_cast<T2 *>(a.table) + off;
-    double e2 = 0.0;
-    for (int j = j0; j < j1; ++j) {
+    __int128 e2i = 0;        // FP32 path: exact sum of ((e_int - mean) >> 8)^2
+    double e2d = 0.0;        // FP64 path
+    for (int j = tid; j < nx; j += nt) {
         const int jm = (j == 0) ? nx - 1 : j - 1, jp = (j == nx - 1) ? 0 : j + 1;
-        const long long ei = s_v[j] - mean_i;
-        const long long btj = (j == 0) ? s_v[0] : s_v[j] - s_v[j - 1];
+        const long long ej_i = s_v[pad_idx(j)];
+        const long long ei = ej_i - mean_i;
+        const long long btj = (j == 0) ? ej_i : ej_i - s_v[pad_idx(j - 1)];
         T2 t;
         if (sizeof(T) == 4) {
             // FP32 table straight from the exact integers; the sub-quantum
             // gauge/remainder terms (< nx quanta) are below FP32 resolution
             const float finv = (float)inv;                   // power of two: exact
-            const float ef = (float)ei * finv;
-            t.x = (T)(-ef);
+            t.x = (T)(-((float)ei * finv));
             if (a.d2_mode == SWPIC_D2_NODAL)
                 t.y = (T)(-(float)btj * finv * (float)R.inv_h);
             else
-                t.y = (T)((float)(s_v[jm] - s_v[jp]) * finv * (float)(0.5 * R.inv_h));
-            e2 += (double)ef * (double)ef;
+                t.y = (T)((float)(s_v[pad_idx(jm)] - s_v[pad_idx(jp)]) * finv * (float)(0.5 * R.inv_h));
+            const long long es = ei >> 8;                    // squares of 2^51 sum safely in int128
+            e2i += (__int128)es * es;
         } else {
             auto efield = [&](int k) {
-                return ((double)(s_v[k] - mean_i) - mfrac) * inv - ((double)(k + 1) - cen) * rem_node;
+                return ((double)(s_v[pad_idx(k)] - mean_i) - mfrac) * inv - ((double)(k + 1) - cen) * rem_node;
             };
             const double ej = efield(j);
             t.x = (T)(-ej);
@@ -227,11 +294,25 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
                 t.y = (T)(-((double)btj * inv - rem_node) * R.inv_h);
             else
                 t.y = (T)((efield(jm) - efield(jp)) * (0.5 * R.inv_h));
-            e2 += ej * ej;
+            e2d += ej * ej;
         }
         tab[j] = t;
     }
-    const double E2 = block_sum_d(e2, sh_d);
+    double E2 = 0.0;
+    if (sizeof(T) == 4) {
+        e2i = warp_sum_i128(e2i);
+        if (lane == 0) s_e2[warp] = e2i;
+        __syncthreads();
+        if (tid == 0) {
+            __int128 t = 0;
+            for (int w = 0; w < (nt >> 5); ++w) t += s_e2[w];
+            const double sc = inv * 256.0;                   // undo the >> 8
+            E2 = (double)t * sc * sc;
+        }
+    } else {
+        __shared__ double sh_d[32];
+        E2 = block_sum_d(e2d, sh_d);
+    }
     if (tid == 0) {
         const double W = 0.5 * R.h * E2;
         const double Ea = sqrt(E2 / (double)nx);
@@ -361,7 +442,7 @@ __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
     P = P - k2 * f.x;
     if (DEC) qs = qs + k2 * ps * d2;
     // drift
-    Q = wrap_pos(Q + kd * P, G.L);
+    Q = drift_wrap(Q, P, kd, G);
     if (DEC) ps = ps - kd * qs;
     if (DEP) {
         key = elem_of(Q, G.inv_h, nx);
@@ -654,7 +735,7 @@ __global__ void __launch_bounds__(1024) k_phi(const RunDev *runs, int n_runs, co
 }
 
 // ---------------------------------------------------------------------------
-size_t solve_smem_bytes(int max_nx) { return (size_t)max_nx * 8; }
+size_t solve_smem_bytes(int max_nx) { return (size_t)(max_nx + max_nx / 32 + 1) * 8; }
 
 size_t pass_smem_bytes(int prec, int max_nx, int mode) {
     const size_t t2 = (prec == SWPIC_F64) ? 16 : 8;
