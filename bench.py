@@ -232,7 +232,9 @@ def main():
         swpic.swpic_refresh(s.ctx)
 
     if args.resort < 0 and not args.no_autotune:
-        swpic.swpic_autotune(sim.ctx, 10, None)
+        # tune on the state the timed region sees (after the warm-up), then restart
+        sim.step(args.warmup, args.diag_every)
+        swpic.swpic_autotune(sim.ctx, 20, None)
     tpb, bpsm, resort = swpic.swpic_get_launch(sim.ctx)
     restore(sim)
 

@@ -1105,17 +1105,21 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
             for (int rs : rss) {
                 ctx->tpb = tpb; ctx->bpsm = bpsm; ctx->resort = rs;
                 clear_graphs(ctx);
+                // a trial covers at least two re-sort intervals so the sort cost is
+                // amortised as in a long run; the score is time per step
+                const int n_trial = std::max(steps_per_trial, rs > 0 ? 2 * rs : 0);
                 float ms = 0.f;
                 for (int rep = 0; rep < 2 && st == SWPIC_OK; ++rep) {
                     st = restore();
                     if (st != SWPIC_OK) break;
                     cudaEventRecord(e0, ctx->stream);
-                    st = swpic_step(ctx, steps_per_trial, 0);
+                    st = swpic_step(ctx, n_trial, 0);
                     cudaEventRecord(e1, ctx->stream);
                     if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, SWPIC_ECUDA, "autotune trial");
                     cudaEventElapsedTime(&ms, e0, e1);
                 }
                 if (st != SWPIC_OK) break;
+                ms /= (float)n_trial;
                 if (ms < best) { best = ms; bt = tpb; bb = bpsm; br = rs; }
             }
         }
@@ -1133,7 +1137,7 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
         std::snprintf(line, sizeof(line),
                       " \"%s\": {\"threads_per_block\": %d, \"blocks_per_sm\": %d, \"resort_every\": %d, "
                       "\"ms_per_step\": %.6g}",
-                      key, bt, bb, br, best / steps_per_trial);
+                      key, bt, bb, br, best);
         std::string body;
         const size_t open = text.find('{'), close = text.rfind('}');
         if (open != std::string::npos && close != std::string::npos && close > open) {

@@ -198,80 +198,106 @@ __device__ __forceinline__ __int128 warp_sum_i128(__int128 v) {
     return v;
 }
 
-// shared-memory index of mesh entry j, padded by one word per 32 so that the
-// contiguous per-lane chunks of the serial part do not all hit one bank
-__device__ __forceinline__ int pad_idx(int j) { return j + (j >> 5); }
-
 template <typename T>
 __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned char *smem, bool full) {
     using T2 = typename Vec2<T>::type;
-    __shared__ long long s_par[4];                 // q, rem, mean_i, (spare)
-    __shared__ double s_mfrac;
-    __shared__ __int128 s_e2[32];
+    __shared__ long long sh_ll[33];
+    __shared__ __int128 sh_q[32];
     const int nx = R.nx, tid = threadIdx.x, nt = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5;
-    long long *s_v = reinterpret_cast<long long *>(smem);      // acc, then e_int (padded)
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    long long *s_p = reinterpret_cast<long long *>(smem);      // raw prefix P_j
     unsigned long long *acc = a.acc + R.mesh_off;
     long long *snap = a.snap + R.mesh_off;
     const int off = R.mesh_off;
+    const int per = (nx + nt - 1) / nt;
+    const int j0 = min(nx, tid * per), j1 = min(nx, j0 + per);
 
-    // 1. all threads: stage acc (coalesced), snapshot it, clear it
-    for (int j = tid; j < nx; j += nt) {
+    // 1. own contiguous chunk: load, snapshot, clear, and its raw sum
+    long long tot = 0;
+    for (int j = j0; j < j1; ++j) {
         const long long v = (long long)__ldcg(acc + j);
-        s_v[pad_idx(j)] = v;
+        s_p[j] = v;
         snap[j] = v;
         if (full) acc[j] = 0ull;
+        tot += v;
     }
     if (!full) return;
+    // 2. one block scan of the raw accumulator gives the total S and P_j
+    long long inc = tot;
+    for (int o = 1; o < 32; o <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) sh_ll[warp] = inc;
     __syncthreads();
-    // 2. warp 0: exact integer neutralisation, Gauss prefix and its mean
     if (warp == 0) {
-        const int per = (nx + 31) >> 5;
-        const int j0 = min(nx, lane * per), j1 = min(nx, j0 + per);
-        long long loc = 0;
-        for (int j = j0; j < j1; ++j) loc += s_v[pad_idx(j)];
-        const long long S = warp_sum_ll(loc);
-        long long q = S / nx, rem = S % nx;
-        if (rem < 0) { rem += nx; q -= 1; }
-        long long tot = 0;
-        for (int j = j0; j < j1; ++j) tot += s_v[pad_idx(j)] - q;
-        long long inc = tot;
+        long long x = (lane < nw) ? sh_ll[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= o) inc += y;
+            const long long y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane >= o) x += y;
         }
-        long long p = inc - tot;
-        __int128 es = 0;
-        for (int j = j0; j < j1; ++j) {
-            p += s_v[pad_idx(j)] - q;
-            s_v[pad_idx(j)] = p;                    // e_int_j
-            es += (__int128)p;
-        }
-        es = warp_sum_i128(es);
-        if (lane == 0) {
-            const double mean = (double)es / (double)nx;
-            const long long mean_i = (long long)floor(mean);
-            s_par[0] = q;
-            s_par[1] = rem;
-            s_par[2] = mean_i;
-            s_mfrac = ((double)(es - (__int128)mean_i * nx)) / (double)nx;
-        }
+        if (lane < nw) sh_ll[lane] = x;                          // inclusive warp totals
+        if (lane == nw - 1) sh_ll[32] = x;                       // S
     }
     __syncthreads();
-    // 3. all threads: table, sum of E^2
-    const long long rem = s_par[1], mean_i = s_par[2];
-    const double mfrac = s_mfrac;
+    const long long S = sh_ll[32];
+    long long q = S / nx, rem = S % nx;                          // S = q nx + rem, 0 <= rem < nx
+    if (rem < 0) { rem += nx; q -= 1; }
+    long long P = ((warp > 0) ? sh_ll[warp - 1] : 0) + inc - tot; // exclusive prefix of my chunk
+    // e_int_j = P_j - (j+1) q  (exact Gauss prefix of btilde_j = acc_j - q), in place
+    __int128 es = 0;
+    for (int j = j0; j < j1; ++j) {
+        P += s_p[j];
+        const long long e = P - (long long)(j + 1) * q;
+        s_p[j] = e;
+        es += (__int128)e;
+    }
+    // 3. gauge: mean of e_int (int128 block sum; its barrier also publishes s_p)
+    {
+        const unsigned long long lo = (unsigned long long)es, hi = (unsigned long long)(es >> 64);
+        unsigned long long l2 = lo, h2 = hi;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ol = __shfl_xor_sync(0xffffffffu, l2, o);
+            const unsigned long long oh = __shfl_xor_sync(0xffffffffu, h2, o);
+            const __int128 t = (__int128)(((unsigned __int128)h2 << 64) | l2) +
+                               (__int128)(((unsigned __int128)oh << 64) | ol);
+            l2 = (unsigned long long)t;
+            h2 = (unsigned long long)(t >> 64);
+        }
+        if (lane == 0) sh_q[warp] = (__int128)(((unsigned __int128)h2 << 64) | l2);
+        (void)lo; (void)hi;
+    }
+    __syncthreads();
+    // mean = esum / nx as an integer part and a fraction, by thread 0 (the
+    // int128 -> double estimate is refined with exact integer arithmetic)
+    if (tid == 0) {
+        __int128 esum = 0;
+        for (int w = 0; w < nw; ++w) esum += sh_q[w];
+        const double est = ((double)(long long)(esum >> 64) * 18446744073709551616.0 +
+                            (double)(unsigned long long)esum) / (double)nx;
+        long long mi = (long long)floor(est);
+        __int128 rr = esum - (__int128)mi * nx;
+        while (rr < 0) { rr += nx; --mi; }
+        while (rr >= nx) { rr -= nx; ++mi; }
+        sh_ll[0] = mi;
+        sh_ll[1] = (long long)rr;
+    }
+    __syncthreads();
+    const long long mean_i = sh_ll[0];
+    const double mfrac = (double)sh_ll[1] / (double)nx;
     const double inv = R.fx_inv;
     const double rem_node = (double)rem * inv / (double)nx;
     const double cen = 0.5 * (double)(nx + 1);
     T2 *tab = reinterpret_cast<T2 *>(a.table) + off;
     __int128 e2i = 0;        // FP32 path: exact sum of ((e_int - mean) >> 8)^2
     double e2d = 0.0;        // FP64 path
-    for (int j = tid; j < nx; j += nt) {
+    for (int j = j0; j < j1; ++j) {
         const int jm = (j == 0) ? nx - 1 : j - 1, jp = (j == nx - 1) ? 0 : j + 1;
-        const long long ej_i = s_v[pad_idx(j)];
+        const long long ej_i = s_p[j];
+        const long long em_i = s_p[jm];
+        const long long ep_i = s_p[jp];
         const long long ei = ej_i - mean_i;
-        const long long btj = (j == 0) ? ej_i : ej_i - s_v[pad_idx(j - 1)];
+        const long long btj = (j == 0) ? ej_i : ej_i - em_i;
         T2 t;
         if (sizeof(T) == 4) {
             // FP32 table straight from the exact integers; the sub-quantum
@@ -281,33 +307,41 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
             if (a.d2_mode == SWPIC_D2_NODAL)
                 t.y = (T)(-(float)btj * finv * (float)R.inv_h);
             else
-                t.y = (T)((float)(s_v[pad_idx(jm)] - s_v[pad_idx(jp)]) * finv * (float)(0.5 * R.inv_h));
-            const long long es = ei >> 8;                    // squares of 2^51 sum safely in int128
-            e2i += (__int128)es * es;
+                t.y = (T)((float)(em_i - ep_i) * finv * (float)(0.5 * R.inv_h));
+            const long long e8 = ei >> 8;                    // squares of 2^51 sum safely in int128
+            e2i += (__int128)e8 * e8;
         } else {
-            auto efield = [&](int k) {
-                return ((double)(s_v[pad_idx(k)] - mean_i) - mfrac) * inv - ((double)(k + 1) - cen) * rem_node;
+            auto efield = [&](long long eint, int kk) {
+                return ((double)(eint - mean_i) - mfrac) * inv - ((double)(kk + 1) - cen) * rem_node;
             };
-            const double ej = efield(j);
+            const double ej = efield(ej_i, j);
             t.x = (T)(-ej);
             if (a.d2_mode == SWPIC_D2_NODAL)
                 t.y = (T)(-((double)btj * inv - rem_node) * R.inv_h);
             else
-                t.y = (T)((efield(jm) - efield(jp)) * (0.5 * R.inv_h));
+                t.y = (T)((efield(em_i, jm) - efield(ep_i, jp)) * (0.5 * R.inv_h));
             e2d += ej * ej;
         }
         tab[j] = t;
     }
+    // 4. W = (h/2) sum E^2, E_amp (thread 0)
     double E2 = 0.0;
     if (sizeof(T) == 4) {
-        e2i = warp_sum_i128(e2i);
-        if (lane == 0) s_e2[warp] = e2i;
+        __int128 t = e2i;
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long ol = __shfl_xor_sync(0xffffffffu, (unsigned long long)t, o);
+            const unsigned long long oh = __shfl_xor_sync(0xffffffffu, (unsigned long long)(t >> 64), o);
+            t += (__int128)(((unsigned __int128)oh << 64) | ol);
+        }
+        __syncthreads();                                     // sh_q reuse
+        if (lane == 0) sh_q[warp] = t;
         __syncthreads();
         if (tid == 0) {
-            __int128 t = 0;
-            for (int w = 0; w < (nt >> 5); ++w) t += s_e2[w];
+            __int128 u = 0;
+            for (int w = 0; w < nw; ++w) u += sh_q[w];
+            const double hi = (double)(long long)(u >> 64), lo = (double)(unsigned long long)u;
             const double sc = inv * 256.0;                   // undo the >> 8
-            E2 = (double)t * sc * sc;
+            E2 = (hi * 18446744073709551616.0 + lo) * sc * sc;
         }
     } else {
         __shared__ double sh_d[32];
@@ -418,7 +452,7 @@ template <typename T, bool DEC, bool DEP, bool DIAG, int D2>
 __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
                                          const typename Vec2<T>::type *tab, const int nx,
                                          const Geo<T> &G, const T k1, const T k2, const T kd,
-                                         Thread<T> &th, int &key, T &w0, T &w1) {
+                                         T &dm, T &dk, int &key, T &w0, T &w1) {
     const int i = elem_of(Q, G.inv_h, nx);
     const auto f = tab[i];
     T d2 = T(0);
@@ -435,8 +469,8 @@ __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
     P = P - k1 * f.x;
     if (DEC) qs = qs + k1 * ps * d2;
     if (DIAG) {
-        th.mom.add(w * P + (DEC ? qs : T(0)));
-        th.kin.add(T(0.5) * w * P * P + (DEC ? qs * P : T(0)));
+        dm = w * P + (DEC ? qs : T(0));                       // momentum density
+        dk = T(0.5) * w * P * P + (DEC ? qs * P : T(0));      // kinetic density
     }
     // opening half-kick of the next step
     P = P - k2 * f.x;
@@ -490,8 +524,9 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
         T Q = Qi[k], P = Pi[k], w = wi[k];
         T qs = DEC ? qsi[k] : T(0), ps = DEC ? psi[k] : T(0);
         int key = -1;
-        T w0 = T(0), w1 = T(0);
-        push_one<T, DEC, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, th, key, w0, w1);
+        T w0 = T(0), w1 = T(0), dm = T(0), dk = T(0);
+        push_one<T, DEC, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, dm, dk, key, w0, w1);
+        if (DIAG) { th.mom.add(dm); th.kin.add(dk); }
         Qo[k] = Q;
         Po[k] = P;
         if (DEC) { qso[k] = qs; pso[k] = ps; }
@@ -536,13 +571,17 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
                 T *Q = reinterpret_cast<T *>(&q[u]), *P = reinterpret_cast<T *>(&p[u]);
                 T *X = reinterpret_cast<T *>(&x[u]), *Y = reinterpret_cast<T *>(&y[u]);
                 const T *M = reinterpret_cast<const T *>(&m[u]);
+                T vm = T(0), vk = T(0);       // the vector's diagnostics, one compensated add each
 #pragma unroll
                 for (int l = 0; l < VW; ++l) {
                     T qs = DEC ? X[l] : T(0), ps = DEC ? Y[l] : T(0);
+                    T dm = T(0), dk = T(0);
                     push_one<T, DEC, DEP, DIAG, D2>(Q[l], P[l], qs, ps, M[l], s_tab, nx, G, k1, k2,
-                                                    kd, th, key[l], w0[l], w1[l]);
+                                                    kd, dm, dk, key[l], w0[l], w1[l]);
+                    if (DIAG) { vm += dm; vk += dk; }
                     if (DEC) { X[l] = qs; Y[l] = ps; }
                 }
+                if (DIAG) { th.mom.add(vm); th.kin.add(vk); }
                 const int64_t vv = vb + u * stride + threadIdx.x;
                 reinterpret_cast<V *>(Qo)[vv] = q[u];
                 reinterpret_cast<V *>(Po)[vv] = p[u];
@@ -613,6 +652,10 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
     T2 *s_tab = reinterpret_cast<T2 *>(smem);
     void *s_mesh = smem + (size_t)a.max_nx * sizeof(T2);
 
+    // Programmatic dependent launch: this grid may be scheduled while the
+    // previous pass's last CTA is still solving; wait for that grid to finish
+    // (and its writes to be visible) before touching any memory.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t c0 = (int64_t)blockIdx.x * a.chunk;
     const int64_t c1 = min(c0 + a.chunk, a.n_total);
     if (c0 >= c1) return;
@@ -640,6 +683,8 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
         th.mom = {T(0), T(0)};
         th.kin = {T(0), T(0)};
         process_segment<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, th, a.err + r);
+        // every CTA has been scheduled by now: let the next pass launch early
+        asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         __syncthreads();
         if (DEP) {
             unsigned long long *gacc = a.acc + R.mesh_off;
@@ -703,8 +748,6 @@ __global__ void __launch_bounds__(1024) k_solve_runs(PassArgs a, int full) {
 __global__ void __launch_bounds__(1024) k_phi(const RunDev *runs, int n_runs, const double *efield,
                                               double *phi) {
     __shared__ double sh[32];
-    __shared__ long long shl[32];
-    (void)shl;
     const int r = blockIdx.x;
     if (r >= n_runs) return;
     const RunDev R = runs[r];
@@ -735,7 +778,7 @@ __global__ void __launch_bounds__(1024) k_phi(const RunDev *runs, int n_runs, co
 }
 
 // ---------------------------------------------------------------------------
-size_t solve_smem_bytes(int max_nx) { return (size_t)(max_nx + max_nx / 32 + 1) * 8; }
+size_t solve_smem_bytes(int max_nx) { return (size_t)max_nx * 8; }
 
 size_t pass_smem_bytes(int prec, int max_nx, int mode) {
     const size_t t2 = (prec == SWPIC_F64) ? 16 : 8;
@@ -755,8 +798,17 @@ static cudaError_t launch_pass_t(const PassArgs &a, int grid, int tpb, size_t sm
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                (int)smem);                                        \
         if (err != cudaSuccess) return err;                                                       \
-        kern<<<grid, tpb, smem, s>>>(a);                                                          \
-        return cudaGetLastError();                                                                \
+        cudaLaunchConfig_t cfg = {};                                                              \
+        cudaLaunchAttribute attr[1];                                                              \
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                          \
+        attr[0].val.programmaticStreamSerializationAllowed = 1;                                   \
+        cfg.gridDim = dim3(grid);                                                                 \
+        cfg.blockDim = dim3(tpb);                                                                 \
+        cfg.dynamicSmemBytes = smem;                                                              \
+        cfg.stream = s;                                                                           \
+        cfg.attrs = attr;                                                                         \
+        cfg.numAttrs = 1;                                                                         \
+        return cudaLaunchKernelEx(&cfg, kern, a);                                                 \
     } while (0)
     if (nodal) {
         if (dep && diag) SWPIC_LAUNCH(true, true, SWPIC_D2_NODAL);
