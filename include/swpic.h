@@ -40,6 +40,7 @@ extern "C" {
 
 #define SWPIC_ABI_VERSION 1
 #define SWPIC_NX_MAX 4096          /* mesh elements per run (shared-memory tile) */
+#define SWPIC_STATIC_NX_MAX 4096   /* mesh elements of swpic_deposit_static */
 
 typedef enum swpic_status {
     SWPIC_OK = 0,
@@ -237,6 +238,32 @@ swpic_status swpic_synchronize(swpic_ctx *ctx);
 /* Synchronous.  flags[r] = anomaly bits of run r (1: fixed-point charge
  * accumulator overflow, 2: non-finite field); n_runs must equal the runs. */
 swpic_status swpic_run_status(swpic_ctx *ctx, int32_t *flags, int32_t n_runs);
+
+/* ---- deposit without device allocation ---------------------------------------- */
+
+/* Mesh charge b_j = sum_a psi*_a phi_j(Q_a) - p*_a phi_j'(Q_a) of one run, for
+ * callers that cannot let this library allocate device memory (for example an
+ * application that owns the whole device-memory budget through its own pool
+ * and forbids other code from calling cudaMalloc/cudaFree).  No counterpart in
+ * the paper: it is a memory-management variant of swpic_deposit + the b of
+ * swpic_get_mesh.  It allocates nothing: its scratch (a fixed-point charge
+ * accumulator of SWPIC_STATIC_NX_MAX int64 words and two doubles, 32 KB per
+ * device) lives in file-scope device arrays that every GPU which loads the
+ * library holds until the process exits.
+ *   Q, ps, psi: caller's device arrays of n elements, float (precision 32) or
+ *               double (64); ps may be NULL (no decoration).
+ *   b:          caller's device array of nx doubles (output).
+ *   L, nx:      the periodic mesh; 2 <= nx <= SWPIC_STATIC_NX_MAX, else
+ *               SWPIC_EINVAL (the scratch holds at most that many nodes).
+ *   stream:     work is enqueued here, asynchronously.
+ * The first call on a device looks up the device addresses of the scratch
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  Every call clears and reuses the same scratch, so calls
+ * whose work overlaps on the GPU (different streams, or different host threads
+ * on one device) race and must be serialised by the caller. */
+swpic_status swpic_deposit_static(const void *Q, const void *ps, const void *psi, int64_t n,
+                                  int32_t precision, double L, int32_t nx, double *b,
+                                  swpic_stream stream);
 
 /* ---- end to end from host memory --------------------------------------------- */
 

@@ -1,0 +1,174 @@
+// swpic_deposit_static: the charge deposit of one run without any device
+// allocation.
+//
+// Who needs this: callers that cannot let a library allocate device memory,
+// e.g. a host application that owns the whole device-memory budget through its
+// own pool or allocator and forbids third-party cudaMalloc/cudaFree, or code
+// that must not touch the allocator at all from a time-critical loop.  The
+// regular path (swpic_create + swpic_deposit) allocates its accumulators when
+// the context is created; this entry point instead keeps its scratch in
+// file-scope device arrays of fixed size that exist as long as the library is
+// loaded (every GPU that loads the library holds them until the process exits).
+//
+// Scratch: SWPIC_STATIC_NX_MAX (4096) int64 words for the fixed-point charge
+// accumulator plus two doubles for the weight bound: 32 KB + 16 B per device.
+//
+// Arithmetic is the same as the context path's deposit: b_j = sum_a psi*_a
+// phi_j(Q_a) - p*_a phi_j'(Q_a) on a periodic P1 mesh, element decided by
+// floor(Q nx/L) in the state's precision, per-thread contributions converted to
+// 64-bit fixed point with a power-of-two scale fixed by sum |psi*| + 2 sum |p*|/h,
+// and added exactly with integer atomics.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <mutex>
+
+#include "swpic.h"
+
+namespace {
+
+constexpr int kStaticNxMax = SWPIC_STATIC_NX_MAX;
+
+// the scratch: it keeps the last call's contents; each call clears it first
+static __device__ __align__(256) unsigned long long g_acc[kStaticNxMax];
+static __device__ __align__(256) double g_bound[2];
+
+struct StaticPtrs {
+    unsigned long long *acc = nullptr;
+    double *bound = nullptr;
+};
+
+std::mutex g_mu;
+StaticPtrs g_ptrs[64];          // per device ordinal
+bool g_ready[64] = {false};
+
+__global__ void k_static_clear(unsigned long long *acc, double *bound, int nx) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j <= nx && j < kStaticNxMax; j += gridDim.x * blockDim.x)
+        acc[j] = 0ull;
+    if (blockIdx.x == 0 && threadIdx.x == 0) { bound[0] = 0.0; bound[1] = 0.0; }
+}
+
+template <typename T>
+__global__ void k_static_bound(const T *ps, const T *psi, int64_t n, double *bound) {
+    double a = 0.0, b = 0.0;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        a += fabs((double)psi[k]);
+        if (ps) b += fabs((double)ps[k]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(bound, a);
+        atomicAdd(bound + 1, b);
+    }
+}
+
+__device__ __forceinline__ float floor_t(float x) { return floorf(x); }
+__device__ __forceinline__ double floor_t(double x) { return floor(x); }
+
+// position inside element i; in FP32 the rounding error of q*inv_h and the low
+// part of nx/L are added back so xi is accurate to its own ulp
+__device__ __forceinline__ float xi_t(float q, int i, float inv_h, float inv_h_lo) {
+    const float p = q * inv_h;
+    return (p - (float)i) + fmaf(q, inv_h_lo, fmaf(q, inv_h, -p));
+}
+__device__ __forceinline__ double xi_t(double q, int i, double inv_h, double) {
+    return q * inv_h - (double)i;
+}
+
+__device__ __forceinline__ double fixed_scale(const double *bound, double inv_h) {
+    const double m = bound[0] + 2.0 * bound[1] * inv_h;
+    int k = 58;
+    if (m > 0.0) k = 58 - (int)ceil(log2(m));
+    k = max(-1000, min(1000, k));
+    return ldexp(1.0, k);
+}
+
+template <typename T>
+__global__ void k_static_deposit(const T *Q, const T *ps, const T *psi, int64_t n, T inv_h, T inv_h_lo,
+                                 int nx, const double *bound, unsigned long long *acc) {
+    extern __shared__ unsigned long long s_mesh[];           // nx + 1 words
+    for (int j = threadIdx.x; j <= nx; j += blockDim.x) s_mesh[j] = 0ull;
+    __syncthreads();
+    const double scale = fixed_scale(bound, (double)inv_h);
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (int64_t)gridDim.x * blockDim.x) {
+        const T q = Q[k];
+        int i = (int)floor_t(q * inv_h);
+        i = max(0, min(nx - 1, i));
+        const T xi = xi_t(q, i, inv_h, inv_h_lo);
+        T w0 = psi[k] * (T(1) - xi), w1 = psi[k] * xi;
+        if (ps) {
+            const T dq = ps[k] * inv_h;
+            w0 += dq;
+            w1 -= dq;
+        }
+        atomicAdd(s_mesh + i, (unsigned long long)__double2ll_rn((double)w0 * scale));
+        atomicAdd(s_mesh + i + 1, (unsigned long long)__double2ll_rn((double)w1 * scale));
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j <= nx; j += blockDim.x) {
+        const unsigned long long v = s_mesh[j];
+        if (v) atomicAdd(acc + (j == nx ? 0 : j), v);
+    }
+}
+
+__global__ void k_static_finish(const unsigned long long *acc, const double *bound, double inv_h, int nx,
+                                double *b) {
+    const double inv = 1.0 / fixed_scale(bound, inv_h);
+    for (int j = threadIdx.x; j < nx; j += blockDim.x) b[j] = (double)(long long)acc[j] * inv;
+}
+
+// once per device, with that device current: the device addresses of the
+// scratch arrays (their host-side names are not device addresses)
+swpic_status static_setup(StaticPtrs *out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SWPIC_ECUDA;
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_ready[dev]) {
+        StaticPtrs p;
+        if (cudaGetSymbolAddress((void **)&p.acc, g_acc) != cudaSuccess) return SWPIC_ECUDA;
+        if (cudaGetSymbolAddress((void **)&p.bound, g_bound) != cudaSuccess) return SWPIC_ECUDA;
+        g_ptrs[dev] = p;
+        g_ready[dev] = true;
+    }
+    *out = g_ptrs[dev];
+    return SWPIC_OK;
+}
+
+}  // namespace
+
+extern "C" swpic_status swpic_deposit_static(const void *Q, const void *ps, const void *psi, int64_t n,
+                                             int32_t precision, double L, int32_t nx, double *b,
+                                             swpic_stream stream) {
+    if (nx < 2 || nx > kStaticNxMax) return SWPIC_EINVAL;        // beyond the static scratch
+    if (!(L > 0.0) || !std::isfinite(L) || n < 0 || !b) return SWPIC_EINVAL;
+    if (precision != SWPIC_F32 && precision != SWPIC_F64) return SWPIC_EINVAL;
+    if (n > 0 && (!Q || !psi)) return SWPIC_EINVAL;
+    StaticPtrs p;
+    swpic_status st = static_setup(&p);
+    if (st != SWPIC_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const double inv_h = (double)nx / L;
+    k_static_clear<<<(nx + 256) / 256, 256, 0, s>>>(p.acc, p.bound, nx);
+    if (n > 0) {
+        const int grid = (int)((n + 255) / 256 < 1216 ? (n + 255) / 256 : 1216);
+        const size_t smem = (size_t)(nx + 1) * 8;
+        if (precision == SWPIC_F64) {
+            k_static_bound<double><<<grid, 256, 0, s>>>((const double *)ps, (const double *)psi, n, p.bound);
+            k_static_deposit<double><<<grid, 256, smem, s>>>((const double *)Q, (const double *)ps,
+                                                             (const double *)psi, n, inv_h, 0.0, nx, p.bound,
+                                                             p.acc);
+        } else {
+            k_static_bound<float><<<grid, 256, 0, s>>>((const float *)ps, (const float *)psi, n, p.bound);
+            const float hi = (float)inv_h, lo = (float)(inv_h - (double)hi);
+            k_static_deposit<float><<<grid, 256, smem, s>>>((const float *)Q, (const float *)ps,
+                                                            (const float *)psi, n, hi, lo, nx, p.bound, p.acc);
+        }
+    }
+    k_static_finish<<<1, 256, 0, s>>>(p.acc, p.bound, inv_h, nx, b);
+    return cudaGetLastError() == cudaSuccess ? SWPIC_OK : SWPIC_ECUDA;
+}

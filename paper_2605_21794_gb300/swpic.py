@@ -80,6 +80,8 @@ SIGNATURES = {
     "swpic_run_status": (C.c_int, [_CTX, C.POINTER(C.c_int32), C.c_int32]),
     "swpic_step_host": (C.c_int, [_CTX, _P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_int64,
                                   C.c_int32, C.c_int32]),
+    "swpic_deposit_static": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_double, C.c_int32,
+                                       _P, _P]),
     "swpic_save": (C.c_int, [_CTX, C.c_char_p]),
     "swpic_load": (C.c_int, [_CTX, C.c_char_p]),
     "swpic_set_launch": (C.c_int, [_CTX, C.c_int32, C.c_int32, C.c_int32]),
@@ -265,6 +267,12 @@ def swpic_step_host(ctx, Q, P, qs, ps, psi, Q_out, P_out, qs_out, ps_out, n, n_s
                     diag_every=0):
     _check(load_library().swpic_step_host(ctx, Q, P, qs, ps, psi, Q_out, P_out, qs_out, ps_out,
                                           int(n), int(n_steps), int(diag_every)), ctx)
+
+
+def swpic_deposit_static(Q, ps, psi, n, precision, L, nx, b, stream):
+    """Device pointers in/out (see include/swpic.h); allocates nothing."""
+    _check(load_library().swpic_deposit_static(Q, ps, psi, int(n), int(precision), float(L),
+                                               int(nx), b, stream))
 
 
 def swpic_save(ctx, path):
