@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the deterministic-mode, e2e, ensemble and CPU-baseline legs")
     ap.add_argument("--side", type=int, default=4096, help="lattice side (4096 = the workload)")
+    ap.add_argument("--launch", default=None, help="TPBxBPSM: fixed launch shape (no autotune)")
+    ap.add_argument("--stages", type=int, default=None, help="bulk-copy stages (0 = register loads; no autotune)")
     return ap.parse_args()
 
 
@@ -231,11 +233,18 @@ def main():
         torch.cuda.synchronize()
         swpic.swpic_refresh(s.ctx)
 
-    if args.resort < 0 and not args.no_autotune:
+    if args.launch:
+        tpb_, bpsm_ = (int(x) for x in args.launch.lower().split("x"))
+        swpic.swpic_set_launch(sim.ctx, tpb_, bpsm_, max(args.resort, 0))
+    if args.stages is not None:
+        swpic.swpic_set_pipeline(sim.ctx, args.stages)
+    fixed = args.launch is not None or args.stages is not None
+    if args.resort < 0 and not args.no_autotune and not fixed:
         # tune on the state the timed region sees (after the warm-up), then restart
         sim.step(args.warmup, args.diag_every)
         swpic.swpic_autotune(sim.ctx, 20, None)
     tpb, bpsm, resort = swpic.swpic_get_launch(sim.ctx)
+    stages = swpic.swpic_get_pipeline(sim.ctx)[1]
     restore(sim)
 
     def barrier():
@@ -297,7 +306,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(spec, args, resort),
-                           launch={"threads_per_block": tpb, "blocks_per_sm": bpsm}),
+                           launch={"threads_per_block": tpb, "blocks_per_sm": bpsm,
+                                   "bulk_copy_stages": stages}),
             "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
 
     if not args.no_extras and rank == 0:
@@ -305,6 +315,7 @@ def main():
         other = 1 - mode
         s2 = make(other, resort)
         swpic.swpic_set_launch(s2.ctx, tpb, bpsm, resort)
+        swpic.swpic_set_pipeline(s2.ctx, stages)
         s2.step(args.warmup, args.diag_every)
         ms2 = timed(s2, args.steps)
         line["other_deposit_mode"] = {

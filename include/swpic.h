@@ -236,7 +236,9 @@ swpic_status swpic_get_keys(swpic_ctx *ctx, int32_t *keys, int64_t n);
 swpic_status swpic_synchronize(swpic_ctx *ctx);
 
 /* Synchronous.  flags[r] = anomaly bits of run r (1: fixed-point charge
- * accumulator overflow, 2: non-finite field); n_runs must equal the runs. */
+ * accumulator overflow, 2: non-finite field, 4: a bounded wait for a bulk
+ * copy ran out, reported by swpic_synchronize as SWPIC_ETIMEOUT); n_runs
+ * must equal the runs. */
 swpic_status swpic_run_status(swpic_ctx *ctx, int32_t *flags, int32_t n_runs);
 
 /* ---- deposit without device allocation ---------------------------------------- */
@@ -295,7 +297,22 @@ swpic_status swpic_set_launch(swpic_ctx *ctx, int32_t threads_per_block,
 swpic_status swpic_get_launch(const swpic_ctx *ctx, int32_t *threads_per_block,
                               int32_t *blocks_per_sm, int32_t *resort_every);
 
-/* Times a small grid of launch shapes and re-sort intervals on the bound
+/* How the particle pass moves particle data (no counterpart in the paper; a
+ * property of this implementation).  stages = 0: each thread loads its
+ * 16-byte vectors into registers.  stages = 2..8: one thread per CTA streams
+ * tiles of blockDim.x vectors per array into shared memory with bulk
+ * asynchronous copies (TMA), up to stages - 1 tiles ahead, and writes the
+ * updated tiles back with bulk copies; the stage count actually used is the
+ * largest <= stages that fits in shared memory at blocks_per_sm CTAs per SM
+ * (register loads when fewer than two fit).  Results do not depend on the
+ * choice beyond the deposit-order freedom of SWPIC_DEPOSIT_ATOMIC.  Default 4.
+ * Invalidates captured graphs.  *effective receives the stage count that the
+ * current launch shape gets (0 = register loads). */
+swpic_status swpic_set_pipeline(swpic_ctx *ctx, int32_t stages);
+swpic_status swpic_get_pipeline(const swpic_ctx *ctx, int32_t *requested, int32_t *effective);
+
+/* Times a small grid of launch shapes, particle-load pipelines and re-sort
+ * intervals on the bound
  * state (which is saved before and restored after, bit for bit) and keeps
  * the fastest.  steps_per_trial > 0.  cache_path: JSON file read before and
  * updated after tuning, keyed by (GPU, precision, decoration, deposit mode,

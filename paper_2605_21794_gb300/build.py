@@ -17,6 +17,8 @@ LIB = os.path.join(OUT_DIR, "libswpic.so")
 SOURCES = ["api.cu", "pass.cu", "sort.cu", "init.cu", "static_deposit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# the particle pass writes its fused multiply-adds out; nothing else is contracted
+PER_SOURCE = {"pass.cu": ["-fmad=false"]}
 
 
 def _nvcc():
@@ -42,7 +44,7 @@ def build(force=False, verbose=False):
         o = os.path.join(OUT_DIR, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            jobs.append([nvcc] + ARCH + FLAGS + ["-c", s, "-o", o])
+            jobs.append([nvcc] + ARCH + FLAGS + PER_SOURCE.get(src, []) + ["-c", s, "-o", o])
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=len(jobs)) as ex:
             res = list(ex.map(lambda c: subprocess.run(c, capture_output=True, text=True), jobs))

@@ -24,6 +24,8 @@ constexpr int64_t kSortChunk = 16384;
 // below the 2^62 conversion limit for decorations that grow after set-up
 constexpr int kFixedBits = 58;
 constexpr uint32_t PASS_NO_WRITE = 1u << 10;   // host-only marker (never sent to the device)
+constexpr int kDefaultStages = 4;
+constexpr size_t kPassStaticSmem = 2048;       // the pass kernel's static shared memory (~1.4 KB), rounded up
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
@@ -42,8 +44,10 @@ struct swpic_ctx {
     int prec = 32;
     bool dec = true;
     int mode = 0, d2 = 0, resort = 0, tpb = 256, bpsm = 4, cap = 4096;
+    int pipe = kDefaultStages;        // requested bulk-copy stages (0: register loads)
     bool graphs = true;
     int dev = 0, nsm = 148;
+    size_t smem_sm = 0, smem_block = 0, smem_reserved = 0;   // device shared-memory limits
     std::string gpu_name;
     std::vector<int> nx, mesh_off;
     int total_mesh = 0, max_nx = 0;
@@ -195,6 +199,20 @@ PassArgs base_args(swpic_ctx *ctx) {
     return a;
 }
 
+// Bulk-copy stages that fit next to the table and the mesh when blocks_per_sm
+// CTAs share one SM: the request, reduced to the shared memory available; 0
+// (register loads) when fewer than two stages fit.
+int pass_stages(const swpic_ctx *ctx) {
+    if (ctx->pipe < 2) return 0;
+    size_t budget = ctx->smem_sm / (size_t)std::max(1, ctx->bpsm);
+    budget = budget > ctx->smem_reserved + kPassStaticSmem ? budget - ctx->smem_reserved - kPassStaticSmem : 0;
+    budget = std::min(budget, ctx->smem_block > kPassStaticSmem ? ctx->smem_block - kPassStaticSmem : 0);
+    int S = 0;
+    for (int k = std::min(ctx->pipe, 8); k >= 2; --k)
+        if (pass_smem_bytes(ctx->prec, ctx->max_nx, ctx->mode, ctx->dec, ctx->tpb, k) <= budget) { S = k; break; }
+    return S;
+}
+
 void pass_shape(const swpic_ctx *ctx, int *grid, int64_t *chunk) {
     const int vw = vec_width(ctx->prec);
     const int64_t gmax = (int64_t)ctx->nsm * ctx->bpsm;
@@ -224,7 +242,8 @@ swpic_status enqueue_pass(swpic_ctx *ctx, double c1, double c2, double cd, uint3
     int64_t chunk;
     pass_shape(ctx, &grid, &chunk);
     a.chunk = chunk;
-    const size_t smem = pass_smem_bytes(ctx->prec, ctx->max_nx, ctx->mode);
+    a.stages = pass_stages(ctx);
+    const size_t smem = pass_smem_bytes(ctx->prec, ctx->max_nx, ctx->mode, ctx->dec, ctx->tpb, a.stages);
     if (ctx->N > 0) {
         CK(launch_pass(ctx->prec, ctx->dec, ctx->mode, a, grid, ctx->tpb, smem, ctx->stream));
         ctx->launches += 1;
@@ -346,6 +365,9 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, ctx->dev) != cudaSuccess) return bail(SWPIC_ECUDA);
     ctx->nsm = prop.multiProcessorCount;
+    ctx->smem_sm = prop.sharedMemPerMultiprocessor;
+    ctx->smem_block = prop.sharedMemPerBlockOptin;
+    ctx->smem_reserved = prop.reservedSharedMemPerBlock;
     ctx->gpu_name = prop.name;
     ctx->nx.resize(R);
     ctx->mesh_off.resize(R);
@@ -725,9 +747,9 @@ swpic_status swpic_step(swpic_ctx *ctx, int32_t n_steps, int32_t diag_every) {
         const int64_t G = period >= 64 ? period : period * ((64 + period - 1) / period);
         while (t + G <= s0 + n && G <= 4096) {
             char key[160];
-            std::snprintf(key, sizeof(key), "G%lld/p%lld/d%d/r%d/t%d/b%d", (long long)G,
+            std::snprintf(key, sizeof(key), "G%lld/p%lld/d%d/r%d/t%d/b%d/s%d", (long long)G,
                           (long long)(t % period), d, can_sort(ctx) ? ctx->resort : 0, ctx->tpb,
-                          ctx->bpsm);
+                          ctx->bpsm, pass_stages(ctx));
             auto it = ctx->graph_cache.find(key);
             if (it == ctx->graph_cache.end()) {
                 if (ctx->graph_cache.size() >= 32) clear_graphs(ctx);
@@ -783,6 +805,11 @@ swpic_status swpic_synchronize(swpic_ctx *ctx) {
             bits |= f[r];
         }
         ctx->reported[r] |= f[r];
+    }
+    if (fresh && (bits & kErrTimeout)) {
+        char msg[256];
+        std::snprintf(msg, sizeof(msg), "a bounded device wait ran out in %d run(s) (first: run %d)", fresh, first);
+        return fail(ctx, SWPIC_ETIMEOUT, msg);
     }
     if (fresh) {
         char msg[256];
@@ -1010,6 +1037,21 @@ swpic_status swpic_get_launch(const swpic_ctx *ctx, int32_t *tpb, int32_t *bpsm,
     return SWPIC_OK;
 }
 
+swpic_status swpic_set_pipeline(swpic_ctx *ctx, int32_t stages) {
+    if (!ctx) return SWPIC_EINVAL;
+    if (stages < 0 || stages == 1 || stages > 8) return fail(ctx, SWPIC_EINVAL, "stages must be 0 or 2..8");
+    ctx->pipe = stages;
+    clear_graphs(ctx);
+    return SWPIC_OK;
+}
+
+swpic_status swpic_get_pipeline(const swpic_ctx *ctx, int32_t *requested, int32_t *effective) {
+    if (!ctx) return SWPIC_EINVAL;
+    if (requested) *requested = ctx->pipe;
+    if (effective) *effective = pass_stages(ctx);
+    return SWPIC_OK;
+}
+
 swpic_status swpic_set_timing(swpic_ctx *ctx, int32_t enable) {
     if (!ctx) return SWPIC_EINVAL;
     ctx->timing = enable != 0;
@@ -1032,7 +1074,8 @@ swpic_status swpic_launch_count(const swpic_ctx *ctx, int64_t *count) {
     return SWPIC_OK;
 }
 
-// Autotuner: threads per block x blocks per SM x re-sort interval, timed with
+// Autotuner: threads per block x blocks per SM x particle loads (bulk-copy
+// pipeline or registers) x re-sort interval, timed with
 // CUDA events on the bound state, which is restored bit for bit afterwards.
 swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char *cache_path) {
     swpic_status s = ensure_prepared(ctx);
@@ -1052,14 +1095,17 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
         const std::string needle = std::string("\"") + key + "\"";
         const size_t at = text.find(needle);
         if (at != std::string::npos) {
-            int tpb = 0, bpsm = 0, rs = -1;
+            int tpb = 0, bpsm = 0, rs = -1, stg = -1;
             const char *p = text.c_str() + at + needle.size();
             const char *a = std::strstr(p, "\"threads_per_block\":");
             const char *b = std::strstr(p, "\"blocks_per_sm\":");
             const char *c = std::strstr(p, "\"resort_every\":");
-            if (a && b && c && std::sscanf(a + 20, "%d", &tpb) == 1 && std::sscanf(b + 16, "%d", &bpsm) == 1 &&
-                std::sscanf(c + 15, "%d", &rs) == 1)
-                return swpic_set_launch(ctx, tpb, bpsm, rs);
+            const char *g = std::strstr(p, "\"pipeline_stages\":");
+            if (a && b && c && g && std::sscanf(a + 20, "%d", &tpb) == 1 && std::sscanf(b + 16, "%d", &bpsm) == 1 &&
+                std::sscanf(c + 15, "%d", &rs) == 1 && std::sscanf(g + 18, "%d", &stg) == 1) {
+                swpic_status q = swpic_set_pipeline(ctx, stg);
+                return q != SWPIC_OK ? q : swpic_set_launch(ctx, tpb, bpsm, rs);
+            }
         }
     }
     // snapshot what a trial changes
@@ -1076,7 +1122,7 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
     CK(cudaMemcpyAsync(rc.data(), ctx->d_ring_count, sizeof(int32_t) * ctx->R, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     const int64_t step0 = ctx->step, last_diag0 = ctx->last_diag_step;
-    const int tpb0 = ctx->tpb, bpsm0 = ctx->bpsm, rs0 = ctx->resort;
+    const int tpb0 = ctx->tpb, bpsm0 = ctx->bpsm, rs0 = ctx->resort, pipe0 = ctx->pipe;
     auto restore = [&]() -> swpic_status {
         for (int k = 0; k < 5; ++k)
             if (snap[k]) CK(cudaMemcpyAsync(ctx->st[k], snap[k], bytes, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -1096,37 +1142,45 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
     const int bpsms[] = {1, 2, 4, 8};
     std::vector<int> rss = {0};
     if (ctx->scratch) { rss.push_back(5); rss.push_back(20); rss.push_back(50); }
+    const int pipes[] = {0, kDefaultStages};
     float best = 1e30f;
-    int bt = tpb0, bb = bpsm0, br = rs0;
+    int bt = tpb0, bb = bpsm0, br = rs0, bp = pipe0;
     swpic_status st = SWPIC_OK;
     for (int tpb : tpbs) {
         for (int bpsm : bpsms) {
             if (tpb * bpsm > 2048) continue;
-            for (int rs : rss) {
-                ctx->tpb = tpb; ctx->bpsm = bpsm; ctx->resort = rs;
-                clear_graphs(ctx);
-                // a trial covers at least two re-sort intervals so the sort cost is
-                // amortised as in a long run; the score is time per step
-                const int n_trial = std::max(steps_per_trial, rs > 0 ? 2 * rs : 0);
-                float ms = 0.f;
-                for (int rep = 0; rep < 2 && st == SWPIC_OK; ++rep) {
-                    st = restore();
+            for (int pipe : pipes) {
+                ctx->tpb = tpb; ctx->bpsm = bpsm; ctx->pipe = pipe;
+                if (pipe > 0 && pass_stages(ctx) == 0) continue;      // no stage fits this shape
+                for (int rs : rss) {
+                    ctx->resort = rs;
+                    clear_graphs(ctx);
+                    // a trial covers at least two re-sort intervals so the sort cost is
+                    // amortised as in a long run; the score is time per step
+                    const int n_trial = std::max(steps_per_trial, rs > 0 ? 2 * rs : 0);
+                    float ms = 0.f;
+                    for (int rep = 0; rep < 2 && st == SWPIC_OK; ++rep) {
+                        st = restore();
+                        if (st != SWPIC_OK) break;
+                        cudaEventRecord(e0, ctx->stream);
+                        st = swpic_step(ctx, n_trial, 0);
+                        cudaEventRecord(e1, ctx->stream);
+                        if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, SWPIC_ECUDA, "autotune trial");
+                        cudaEventElapsedTime(&ms, e0, e1);
+                    }
                     if (st != SWPIC_OK) break;
-                    cudaEventRecord(e0, ctx->stream);
-                    st = swpic_step(ctx, n_trial, 0);
-                    cudaEventRecord(e1, ctx->stream);
-                    if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, SWPIC_ECUDA, "autotune trial");
-                    cudaEventElapsedTime(&ms, e0, e1);
+                    ms /= (float)n_trial;
+                    if (ms < best) { best = ms; bt = tpb; bb = bpsm; br = rs; bp = pipe; }
                 }
                 if (st != SWPIC_OK) break;
-                ms /= (float)n_trial;
-                if (ms < best) { best = ms; bt = tpb; bb = bpsm; br = rs; }
             }
+            if (st != SWPIC_OK) break;
         }
+        if (st != SWPIC_OK) break;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->tpb = bt; ctx->bpsm = bb; ctx->resort = br;
+    ctx->tpb = bt; ctx->bpsm = bb; ctx->resort = br; ctx->pipe = bp;
     clear_graphs(ctx);
     swpic_status rs_ = restore();
     for (void *p : snap) if (p) cudaFree(p);
@@ -1136,8 +1190,8 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
         char line[768];
         std::snprintf(line, sizeof(line),
                       " \"%s\": {\"threads_per_block\": %d, \"blocks_per_sm\": %d, \"resort_every\": %d, "
-                      "\"ms_per_step\": %.6g}",
-                      key, bt, bb, br, best);
+                      "\"pipeline_stages\": %d, \"ms_per_step\": %.6g}",
+                      key, bt, bb, br, bp, best);
         std::string body;
         const size_t open = text.find('{'), close = text.rfind('}');
         if (open != std::string::npos && close != std::string::npos && close > open) {

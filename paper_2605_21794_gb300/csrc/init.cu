@@ -104,69 +104,106 @@ __global__ void k_convert(const double *src, T *dst, int64_t n) {
         dst[k] = (T)src[k];
 }
 
-// per chunk: Neumaier sums of psi*, |psi*| and |p*| in FP64, combined in fixed order
+// per chunk: psi* summed as an unevaluated FP32 pair (hi + lo, Knuth's two-sum,
+// error-free per addition) in FP32 state, in FP64 in FP64 state; |psi*| and |p*|
+// (only a bound for the fixed-point scale) as plain sums.  Partial sums are
+// combined in a fixed order, so the result depends only on the run's own data.
+__device__ __forceinline__ void two_sum_acc(float &hi, float &lo, float x) {
+    const float s = hi + x;
+    const float bp = s - hi;
+    const float err = (hi - (s - bp)) + (x - bp);
+    hi = s;
+    lo += err;
+}
+
 template <typename T>
-__device__ __forceinline__ void neumaier(double &s, double &c, double x) {
-    const double t = s + x;
-    c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
-    s = t;
+struct MassAcc {
+    double s = 0.0, sa = 0.0, sp = 0.0;
+    __device__ __forceinline__ void add(T x, T p) {
+        s += x;
+        sa += fabs(x);
+        sp += fabs(p);
+    }
+    __device__ __forceinline__ void get(double &a, double &b, double &c) const { a = s; b = sa; c = sp; }
+};
+
+template <>
+struct MassAcc<float> {
+    float hi = 0.f, lo = 0.f, sa = 0.f, sp = 0.f;
+    __device__ __forceinline__ void add(float x, float p) {
+        two_sum_acc(hi, lo, x);
+        sa += fabsf(x);
+        sp += fabsf(p);
+    }
+    __device__ __forceinline__ void get(double &a, double &b, double &c) const {
+        a = (double)hi + (double)lo;
+        b = (double)sa;
+        c = (double)sp;
+    }
+};
+
+__device__ __forceinline__ void block_sum3(double &a, double &b, double &c, double (*sh)[32]) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+    }
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    if ((threadIdx.x & 31) == 0) { sh[0][w] = a; sh[1][w] = b; sh[2][w] = c; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        a = b = c = 0.0;
+        for (int k = 0; k < nw; ++k) { a += sh[0][k]; b += sh[1][k]; c += sh[2][k]; }
+    }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_mass_partial(const T *psi, const T *ps,
                                                       const SortChunk *chunks, double *partials) {
-    __shared__ double sh[3][8];
+    __shared__ double sh[3][32];
     const SortChunk c = chunks[blockIdx.x];
-    double s = 0.0, cs = 0.0, sa = 0.0, ca = 0.0, sp = 0.0, cp = 0.0;
-    for (int64_t k = c.start + threadIdx.x; k < c.end; k += blockDim.x) {
-        const double x = (double)psi[k];
-        neumaier<T>(s, cs, x);
-        neumaier<T>(sa, ca, fabs(x));
-        if (ps) neumaier<T>(sp, cp, fabs((double)ps[k]));
-    }
-    s += cs;
-    sa += ca;
-    sp += cp;
-    for (int o = 16; o > 0; o >>= 1) {
-        s += __shfl_xor_sync(0xffffffffu, s, o);
-        sa += __shfl_xor_sync(0xffffffffu, sa, o);
-        sp += __shfl_xor_sync(0xffffffffu, sp, o);
-    }
-    if ((threadIdx.x & 31) == 0) {
-        sh[0][threadIdx.x >> 5] = s;
-        sh[1][threadIdx.x >> 5] = sa;
-        sh[2][threadIdx.x >> 5] = sp;
-    }
-    __syncthreads();
+    MassAcc<T> acc;
+    for (int64_t k = c.start + threadIdx.x; k < c.end; k += blockDim.x)
+        acc.add(psi[k], ps ? ps[k] : T(0));
+    double a, b, d;
+    acc.get(a, b, d);
+    block_sum3(a, b, d, sh);
     if (threadIdx.x == 0) {
-        double a = 0.0, b = 0.0, d = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += sh[0][w]; b += sh[1][w]; d += sh[2][w]; }
         partials[3 * blockIdx.x] = a;
         partials[3 * blockIdx.x + 1] = b;
         partials[3 * blockIdx.x + 2] = d;
     }
 }
 
-// mass[r] = sum psi*; bound[r] = (sum |psi*|, sum |p*|)
-__global__ void k_mass_final(const double *partials, const SortChunk *chunks, int n_chunks,
-                             int n_runs, double *mass, double *bound) {
-    const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= n_runs) return;
-    double a = 0.0, b = 0.0, d = 0.0;
-    // chunks are ordered by run: binary search the first chunk of run r
-    int lo = 0, hi = n_chunks;
-    while (lo < hi) {
-        int mid = (lo + hi) >> 1;
-        if (chunks[mid].run < r) lo = mid + 1; else hi = mid;
+// one block per run: mass[r] = sum psi*; bound[r] = (sum |psi*|, sum |p*|)
+__global__ void __launch_bounds__(256) k_mass_final(const double *partials, const SortChunk *chunks,
+                                                    int n_chunks, double *mass, double *bound) {
+    __shared__ double sh[3][32];
+    __shared__ int s_lo;
+    const int r = blockIdx.x;
+    if (threadIdx.x == 0) {
+        // chunks are ordered by run: binary search the first chunk of run r
+        int lo = 0, hi = n_chunks;
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (chunks[mid].run < r) lo = mid + 1; else hi = mid;
+        }
+        s_lo = lo;
     }
-    for (int c = lo; c < n_chunks && chunks[c].run == r; ++c) {
+    __syncthreads();
+    const int lo = s_lo;
+    double a = 0.0, b = 0.0, d = 0.0;
+    for (int c = lo + threadIdx.x; c < n_chunks && chunks[c].run == r; c += blockDim.x) {
         a += partials[3 * c];
         b += partials[3 * c + 1];
         d += partials[3 * c + 2];
     }
-    mass[r] = a;
-    bound[2 * r] = b;
-    bound[2 * r + 1] = d;
+    block_sum3(a, b, d, sh);
+    if (threadIdx.x == 0) {
+        mass[r] = a;
+        bound[2 * r] = b;
+        bound[2 * r + 1] = d;
+    }
 }
 
 cudaError_t launch_init_lattice(int prec, bool decorated, void *Q, void *P, void *qs, void *ps,
@@ -229,7 +266,7 @@ cudaError_t launch_mass(int prec, const void *psi, const void *ps, const SortChu
             k_mass_partial<float><<<n_chunks, 256, 0, s>>>((const float *)psi, (const float *)ps,
                                                            chunks, partials);
     }
-    k_mass_final<<<(n_runs + 127) / 128, 128, 0, s>>>(partials, chunks, n_chunks, n_runs, mass, bound);
+    if (n_runs > 0) k_mass_final<<<n_runs, 256, 0, s>>>(partials, chunks, n_chunks, mass, bound);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,10 @@
 // The particle pass of the decorated-particle step (sm_103a), and the per-run
 // field solve that the last CTA of each run performs at the end of a pass.
 //
+// Floating-point contraction is off for this file (-fmad=false): every fused
+// multiply-add is written as fma(), so each copy of the particle arithmetic
+// (register-load and bulk-copy streams) rounds identically.
+//
 // One pass over the particles of every run does, per particle (Sec. 5,
 // Eq. sw-evolution, with the canonical kick/drift split):
 //   i      = clamp(floor(Q * nx/L), 0, nx-1)                       element of Q
@@ -87,7 +91,7 @@ __device__ __forceinline__ T wrap_pos(T Q, T L) {
 // Drift with the periodic wrap, Q' = Q + kd P mod L.
 // FP64: the domain length is the double L itself.
 __device__ __forceinline__ double drift_wrap(double Q, double P, double kd, const Geo<double> &G) {
-    return wrap_pos(Q + kd * P, G.L);
+    return wrap_pos(fma(kd, P, Q), G.L);
 }
 // FP32: L is not a float; it is carried as L = L_hi + L_lo (L_hi = fl32(L)).
 // Inside-test and shifts use both parts, and a crossing of L is formed from
@@ -426,7 +430,9 @@ __device__ __forceinline__ void mesh_add(int key, T a0, T a1, void *mesh, double
 // Warp-aggregated deposit: lanes holding the same element in consecutive lanes
 // form a segment; a segmented suffix sum (5 shuffle steps, fixed order) gives
 // the segment's first lane the segment total, and only that lane touches the
-// shared mesh.  key < 0 marks an empty slot.  All 32 lanes must call this.
+// shared mesh.  When no lane shares its element with the lane before (a
+// disordered plasma) the shuffles are skipped and every lane adds its own
+// value.  key < 0 marks an empty slot.  All 32 lanes must call this.
 template <typename T, int MODE>
 __device__ __forceinline__ void warp_deposit(int key, T a0, T a1, void *mesh, double scale,
                                              int32_t *err) {
@@ -435,13 +441,15 @@ __device__ __forceinline__ void warp_deposit(int key, T a0, T a1, void *mesh, do
     const int prev = __shfl_up_sync(full, key, 1);
     const bool head = (lane == 0) || (prev != key);
     const unsigned heads = __ballot_sync(full, head);
-    const unsigned above = (lane == 31) ? 0u : (heads & (0xffffffffu << (lane + 1)));
-    const int seg_end = above ? (__ffs(above) - 2) : 31;
+    if (heads != full) {
+        const unsigned above = (lane == 31) ? 0u : (heads & (0xffffffffu << (lane + 1)));
+        const int seg_end = above ? (__ffs(above) - 2) : 31;
 #pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const T b0 = __shfl_down_sync(full, a0, off);
-        const T b1 = __shfl_down_sync(full, a1, off);
-        if (lane + off <= seg_end) { a0 += b0; a1 += b1; }
+        for (int off = 1; off < 32; off <<= 1) {
+            const T b0 = __shfl_down_sync(full, a0, off);
+            const T b1 = __shfl_down_sync(full, a1, off);
+            if (lane + off <= seg_end) { a0 += b0; a1 += b1; }
+        }
     }
     if (head && key >= 0) mesh_add<T, MODE>(key, a0, a1, mesh, scale, err);
 }
@@ -460,33 +468,34 @@ __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
         if (D2 == SWPIC_D2_NODAL) {
             const T xi = xi_of(Q, i, G);
             const T g1 = tab[i + 1 == nx ? 0 : i + 1].y;
-            d2 = f.y + xi * (g1 - f.y);
+            d2 = fma(xi, g1 - f.y, f.y);
         } else {
             d2 = f.y;
         }
     }
     // closing half-kick of the previous step
-    P = P - k1 * f.x;
-    if (DEC) qs = qs + k1 * ps * d2;
+    P = fma(-k1, f.x, P);
+    if (DEC) qs = fma(k1 * ps, d2, qs);
     if (DIAG) {
-        dm = w * P + (DEC ? qs : T(0));                       // momentum density
-        dk = T(0.5) * w * P * P + (DEC ? qs * P : T(0));      // kinetic density
+        dm = DEC ? fma(w, P, qs) : w * P;                                 // momentum density
+        dk = DEC ? fma(T(0.5) * w * P, P, qs * P) : T(0.5) * w * P * P;  // kinetic density
     }
     // opening half-kick of the next step
-    P = P - k2 * f.x;
-    if (DEC) qs = qs + k2 * ps * d2;
+    P = fma(-k2, f.x, P);
+    if (DEC) qs = fma(k2 * ps, d2, qs);
     // drift
     Q = drift_wrap(Q, P, kd, G);
-    if (DEC) ps = ps - kd * qs;
+    if (DEC) ps = fma(-kd, qs, ps);
     if (DEP) {
         key = elem_of(Q, G.inv_h, nx);
         const T xi = xi_of(Q, key, G);
-        w0 = w * (T(1) - xi);
-        w1 = w * xi;
         if (DEC) {
             const T dq = ps * G.inv_h;
-            w0 += dq;
-            w1 -= dq;
+            w0 = fma(w, T(1) - xi, dq);
+            w1 = fma(w, xi, -dq);
+        } else {
+            w0 = w * (T(1) - xi);
+            w1 = w * xi;
         }
     }
 }
@@ -498,6 +507,79 @@ __device__ __forceinline__ int find_run(const RunDev *runs, int n_runs, int64_t 
         if (runs[mid].p0 <= idx) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// Deposit slots of one 16-byte vector of particles: element and node weights.
+template <typename T>
+struct VecOut {
+    static constexpr int n = Vec16<T>::n;
+    int key[n];
+    T w0[n], w1[n];
+    __device__ __forceinline__ void clear() {
+#pragma unroll
+        for (int l = 0; l < n; ++l) { key[l] = -1; w0[l] = T(0); w1[l] = T(0); }
+    }
+};
+
+// Push the particles of one 16-byte vector in place; their diagnostics go to
+// th (one compensated add per vector), their deposit slots to o.
+template <typename T, bool DEC, bool DEP, bool DIAG, int D2>
+__device__ __forceinline__ void push_vector(typename Vec16<T>::type &q, typename Vec16<T>::type &p,
+                                            typename Vec16<T>::type &x, typename Vec16<T>::type &y,
+                                            const typename Vec16<T>::type &m,
+                                            const typename Vec2<T>::type *s_tab, int nx, const Geo<T> &G,
+                                            T k1, T k2, T kd, Thread<T> &th, VecOut<T> &o) {
+    constexpr int VW = Vec16<T>::n;
+    T *Q = reinterpret_cast<T *>(&q), *P = reinterpret_cast<T *>(&p);
+    T *X = reinterpret_cast<T *>(&x), *Y = reinterpret_cast<T *>(&y);
+    const T *M = reinterpret_cast<const T *>(&m);
+    T vm = T(0), vk = T(0);
+#pragma unroll
+    for (int l = 0; l < VW; ++l) {
+        T qs = DEC ? X[l] : T(0), ps = DEC ? Y[l] : T(0);
+        T dm = T(0), dk = T(0);
+        push_one<T, DEC, DEP, DIAG, D2>(Q[l], P[l], qs, ps, M[l], s_tab, nx, G, k1, k2, kd, dm, dk,
+                                        o.key[l], o.w0[l], o.w1[l]);
+        if (DIAG) { vm += dm; vk += dk; }
+        if (DEC) { X[l] = qs; Y[l] = ps; }
+    }
+    if (DIAG) { th.mom.add(vm); th.kin.add(vk); }
+}
+
+// Deposit one vector per lane.  Runs of equal elements inside the vector are
+// summed in registers first (fixed order); the first run of every lane joins
+// one warp-aggregated deposit (so a sorted or cold plasma, where whole
+// vectors share an element, costs one shared atomic per segment of lanes),
+// later runs go to the mesh directly.  All lanes of the warp must call this.
+template <typename T, int MODE>
+__device__ __forceinline__ void deposit_vector(const VecOut<T> &o, void *s_mesh, double scale, int32_t *err) {
+    constexpr int VW = Vec16<T>::n;
+    const int k0 = o.key[0];
+    T s0 = o.w0[0], s1 = o.w1[0];
+    bool first = true;
+    int kr = -1;
+    T r0 = T(0), r1 = T(0);
+#pragma unroll
+    for (int l = 1; l < VW; ++l) {
+        const int k = o.key[l];
+        if (first && k == k0) {
+            s0 += o.w0[l];
+            s1 += o.w1[l];
+        } else {
+            first = false;
+            if (k == kr) {
+                r0 += o.w0[l];
+                r1 += o.w1[l];
+            } else {
+                if (kr >= 0) mesh_add<T, MODE>(kr, r0, r1, s_mesh, scale, err);
+                kr = k;
+                r0 = o.w0[l];
+                r1 = o.w1[l];
+            }
+        }
+    }
+    if (kr >= 0) mesh_add<T, MODE>(kr, r0, r1, s_mesh, scale, err);
+    warp_deposit<T, MODE>(k0, s0, s1, s_mesh, scale, err);
 }
 
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
@@ -565,23 +647,9 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            int key[VW];
-            T w0[VW], w1[VW];
+            VecOut<T> o;
             if (ok[u]) {
-                T *Q = reinterpret_cast<T *>(&q[u]), *P = reinterpret_cast<T *>(&p[u]);
-                T *X = reinterpret_cast<T *>(&x[u]), *Y = reinterpret_cast<T *>(&y[u]);
-                const T *M = reinterpret_cast<const T *>(&m[u]);
-                T vm = T(0), vk = T(0);       // the vector's diagnostics, one compensated add each
-#pragma unroll
-                for (int l = 0; l < VW; ++l) {
-                    T qs = DEC ? X[l] : T(0), ps = DEC ? Y[l] : T(0);
-                    T dm = T(0), dk = T(0);
-                    push_one<T, DEC, DEP, DIAG, D2>(Q[l], P[l], qs, ps, M[l], s_tab, nx, G, k1, k2,
-                                                    kd, dm, dk, key[l], w0[l], w1[l]);
-                    if (DIAG) { vm += dm; vk += dk; }
-                    if (DEC) { X[l] = qs; Y[l] = ps; }
-                }
-                if (DIAG) { th.mom.add(vm); th.kin.add(vk); }
+                push_vector<T, DEC, DEP, DIAG, D2>(q[u], p[u], x[u], y[u], m[u], s_tab, nx, G, k1, k2, kd, th, o);
                 const int64_t vv = vb + u * stride + threadIdx.x;
                 reinterpret_cast<V *>(Qo)[vv] = q[u];
                 reinterpret_cast<V *>(Po)[vv] = p[u];
@@ -591,27 +659,217 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
                 }
                 if (wpsi) reinterpret_cast<V *>(wo)[vv] = m[u];
             } else {
-#pragma unroll
-                for (int l = 0; l < VW; ++l) { key[l] = -1; w0[l] = T(0); w1[l] = T(0); }
+                o.clear();
             }
-            if (DEP) {
-                bool one = true;
-#pragma unroll
-                for (int l = 1; l < VW; ++l) one = one && (key[l] == key[0]);
-                if (__all_sync(0xffffffffu, one)) {
-                    T s0 = w0[0], s1 = w1[0];
-#pragma unroll
-                    for (int l = 1; l < VW; ++l) { s0 += w0[l]; s1 += w1[l]; }
-                    warp_deposit<T, MODE>(key[0], s0, s1, s_mesh, scale, err);
-                } else {
-#pragma unroll
-                    for (int l = 0; l < VW; ++l)
-                        warp_deposit<T, MODE>(key[l], w0[l], w1[l], s_mesh, scale, err);
-                }
-            }
+            if (DEP) deposit_vector<T, MODE>(o, s_mesh, scale, err);
         }
     }
     for (int64_t k = ve + threadIdx.x; k < e; k += blockDim.x) scalar(k);
+}
+
+// ---------------------------------------------------------------------------
+// Bulk-copy (TMA) staged particle stream
+// ---------------------------------------------------------------------------
+// Every warp streams its own particles: in its k-th turn warp w handles the
+// 32 vectors v0 + k blockDim.x + 32 w + [0, 32) of every array (the vectors
+// the register-load loop gives its lanes, in the same order).  Lane 0 copies
+// them global -> shared with cp.async.bulk (one copy of <= 512 B per array,
+// completion counted in bytes on the warp's mbarrier of that stage), S turns
+// ahead; as soon as the lanes have read a stage into registers (__syncwarp)
+// it is refilled with the turn S places further on, while the lanes push,
+// store (plain 16-byte stores) and deposit.  Warps never wait for each other,
+// so one warp's shared atomics overlap another's arithmetic, and the copy
+// engine keeps S x 32 x 16 B per array and warp in flight without registers.
+//
+// Every wait is bounded (kWaitLimitNs of wall time); a wait that runs out
+// sets kErrTimeout in the run's flag word, and the warp stops, waits (again
+// bounded) for its copies in flight, and the CTA leaves the kernel after the
+// segment.
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
+constexpr int kWarpTile = 32;        // vectors per array in one warp turn
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+// true when the phase with this parity completed; false after kWaitLimitNs
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait(bar, parity))
+        if (global_ns() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+__device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_addr(dst_smem)),
+                 "l"(src), "r"(bytes), "r"(smem_addr(bar))
+                 : "memory");
+}
+
+template <typename T, int MODE>
+__host__ __device__ __forceinline__ size_t mesh_bytes(int max_nx) {
+    return (size_t)(max_nx + 1) * (MODE == SWPIC_DEPOSIT_ATOMIC ? sizeof(T) : sizeof(unsigned long long));
+}
+
+// Shared-memory layout of the pass: table | mesh | (bulk stream) mbarriers | stages.
+__host__ __device__ __forceinline__ size_t round128(size_t x) { return (x + 127) / 128 * 128; }
+__host__ __device__ __forceinline__ size_t bar_offset(size_t tab_bytes, size_t mesh_b) {
+    return round128(tab_bytes + mesh_b);
+}
+__host__ __device__ __forceinline__ size_t stage_area_offset(size_t tab_bytes, size_t mesh_b, int nwarps, int S) {
+    return bar_offset(tab_bytes, mesh_b) + round128((size_t)nwarps * S * sizeof(uint64_t));
+}
+
+// Pipeline bookkeeping of one warp; seq counts the warp's turns over the CTA's
+// lifetime, so the stage of a turn is seq % S and its mbarrier parity (seq / S) & 1.
+struct Pipe {
+    unsigned char *base;     // this warp's S stages of n_arr x kWarpTile x 16 bytes
+    uint64_t *bar;           // this warp's S mbarriers
+    int S;
+    uint32_t seq;
+};
+
+template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
+__device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t s, int64_t e,
+                                     const typename Vec2<T>::type *s_tab, void *s_mesh, Thread<T> &th,
+                                     int32_t *err, Pipe &pp, int *s_abort) {
+    using V = typename Vec16<T>::type;
+    constexpr int VW = Vec16<T>::n;
+    constexpr int NA = DEC ? 5 : 3;                       // Q, P, w [, q*, p*]
+    constexpr uint32_t ARR = kWarpTile * sizeof(V);       // bytes per array in a stage
+    const unsigned full = 0xffffffffu;
+    const Geo<T> G = geo_of(R, T());
+    const int nx = R.nx;
+    const T k1 = (T)(a.c1 * R.dt), k2 = (T)(a.c2 * R.dt), kd = (T)(a.cd * R.dt);
+    const double scale = R.fx_scale;
+    const bool wpsi = (a.flags & PASS_WRITE_PSI) != 0;
+    const T *Qi = reinterpret_cast<const T *>(a.Qi), *Pi = reinterpret_cast<const T *>(a.Pi);
+    const T *qsi = reinterpret_cast<const T *>(a.qsi), *psi = reinterpret_cast<const T *>(a.psi_i);
+    const T *wi = reinterpret_cast<const T *>(a.wi);
+    T *Qo = reinterpret_cast<T *>(a.Qo), *Po = reinterpret_cast<T *>(a.Po);
+    T *qso = reinterpret_cast<T *>(a.qso), *pso = reinterpret_cast<T *>(a.pso);
+    T *wo = reinterpret_cast<T *>(a.wo);
+    const T *src[5] = {Qi, Pi, wi, qsi, psi};
+
+    auto scalar = [&](int64_t k) {
+        T Q = Qi[k], P = Pi[k], w = wi[k];
+        T qs = DEC ? qsi[k] : T(0), ps = DEC ? psi[k] : T(0);
+        int key = -1;
+        T w0 = T(0), w1 = T(0), dm = T(0), dk = T(0);
+        push_one<T, DEC, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, dm, dk, key, w0, w1);
+        if (DIAG) { th.mom.add(dm); th.kin.add(dk); }
+        Qo[k] = Q;
+        Po[k] = P;
+        if (DEC) { qso[k] = qs; pso[k] = ps; }
+        if (wpsi) wo[k] = w;
+        if (DEP) mesh_add<T, MODE>(key, w0, w1, s_mesh, scale, err);
+    };
+
+    const int64_t vs = (s + VW - 1) / VW * VW;
+    const int64_t ve = e / VW * VW;
+    if (vs >= ve) {
+        for (int64_t k = s + threadIdx.x; k < e; k += blockDim.x) scalar(k);
+        return true;
+    }
+    for (int64_t k = s + threadIdx.x; k < vs; k += blockDim.x) scalar(k);
+
+    const int64_t v0 = vs / VW, v1 = ve / VW;
+    const int lane = threadIdx.x & 31;
+    const int64_t wbase = v0 + (threadIdx.x - lane);       // first vector of this warp's turn 0
+    const int64_t stride = blockDim.x;
+    const int nturn = wbase < v1 ? (int)((v1 - wbase + stride - 1) / stride) : 0;
+    const int S = pp.S;
+
+    auto turn_vecs = [&](int k) -> int { return (int)min((int64_t)kWarpTile, v1 - (wbase + (int64_t)k * stride)); };
+    auto issue = [&](int k) {            // lane 0 only
+        const uint32_t q = pp.seq + (uint32_t)k;
+        unsigned char *st = pp.base + (size_t)(q % S) * NA * ARR;
+        uint64_t *bar = pp.bar + (q % S);
+        const uint32_t nb = (uint32_t)turn_vecs(k) * (uint32_t)sizeof(V);
+        mbar_arrive_expect_tx(bar, nb * NA);
+        const int64_t gv = wbase + (int64_t)k * stride;
+#pragma unroll
+        for (int j = 0; j < NA; ++j) bulk_load(st + j * ARR, reinterpret_cast<const V *>(src[j]) + gv, nb, bar);
+    };
+
+    if (lane == 0)
+        for (int k = 0; k < S && k < nturn; ++k) issue(k);
+    int issued = min(S, nturn);
+    bool ok = true;
+    int k = 0;
+    for (; k < nturn; ++k) {
+        const uint32_t q = pp.seq + (uint32_t)k;
+        const V *sv = reinterpret_cast<const V *>(pp.base + (size_t)(q % S) * NA * ARR);
+        const bool arrived = mbar_wait_bounded(pp.bar + (q % S), (q / S) & 1u);
+        if (!__all_sync(full, arrived)) {
+            if (lane == 0) { atomicOr(err, kErrTimeout); *s_abort = 1; }
+            ok = false;
+            break;
+        }
+        const bool have = lane < turn_vecs(k);
+        V qv, pv, mv, xv, yv;
+        if (have) {
+            qv = sv[lane];
+            pv = sv[kWarpTile + lane];
+            mv = sv[2 * kWarpTile + lane];
+            if (DEC) { xv = sv[3 * kWarpTile + lane]; yv = sv[4 * kWarpTile + lane]; }
+        }
+        __syncwarp();                    // the stage has been read: refill it
+        if (k + S < nturn) {
+            if (lane == 0) issue(k + S);
+            ++issued;
+        }
+        VecOut<T> o;
+        if (have) {
+            push_vector<T, DEC, DEP, DIAG, D2>(qv, pv, xv, yv, mv, s_tab, nx, G, k1, k2, kd, th, o);
+            const int64_t vv = wbase + (int64_t)k * stride + lane;
+            reinterpret_cast<V *>(Qo)[vv] = qv;
+            reinterpret_cast<V *>(Po)[vv] = pv;
+            if (DEC) {
+                reinterpret_cast<V *>(qso)[vv] = xv;
+                reinterpret_cast<V *>(pso)[vv] = yv;
+            }
+            if (wpsi) reinterpret_cast<V *>(wo)[vv] = mv;
+        } else {
+            o.clear();
+        }
+        if (DEP) deposit_vector<T, MODE>(o, s_mesh, scale, err);
+    }
+    if (!ok && lane == 0) {
+        // drain: wait (bounded) for every copy still in flight into this warp's stages
+        for (int u = k; u < issued; ++u) {
+            const uint32_t qq = pp.seq + (uint32_t)u;
+            mbar_wait_bounded(pp.bar + (qq % S), (qq / S) & 1u);
+        }
+    }
+    pp.seq += (uint32_t)issued;
+    if (ok)         // same per-thread order as the register path: head, vectors, tail
+        for (int64_t kk = ve + threadIdx.x; kk < e; kk += blockDim.x) scalar(kk);
+    __syncthreads();
+    return *s_abort == 0;
 }
 
 template <typename T>
@@ -646,11 +904,28 @@ __device__ void finish_run(const PassArgs &a, const RunDev &R, int r, unsigned c
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
 __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
     using T2 = typename Vec2<T>::type;
-    extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ int s_last;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ int s_last, s_abort;
     __shared__ double s_red[64];
     T2 *s_tab = reinterpret_cast<T2 *>(smem);
     void *s_mesh = smem + (size_t)a.max_nx * sizeof(T2);
+    const bool bulk = a.stages >= 2;
+    Pipe pp;
+    {
+        const size_t tb = (size_t)a.max_nx * sizeof(T2), mb = mesh_bytes<T, MODE>(a.max_nx);
+        const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
+        constexpr size_t stage_bytes = (DEC ? 5 : 3) * kWarpTile * 16;
+        pp.S = a.stages;
+        pp.seq = 0;
+        pp.bar = reinterpret_cast<uint64_t *>(smem + bar_offset(tb, mb)) + (size_t)w * pp.S;
+        pp.base = smem + stage_area_offset(tb, mb, nw, pp.S) + (size_t)w * pp.S * stage_bytes;
+    }
+    if (threadIdx.x == 0) s_abort = 0;
+    if (bulk && (threadIdx.x & 31) == 0) {
+        for (int k = 0; k < pp.S; ++k) mbar_init(pp.bar + k, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
     // Programmatic dependent launch: this grid may be scheduled while the
     // previous pass's last CTA is still solving; wait for that grid to finish
@@ -682,7 +957,13 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
         Thread<T> th;
         th.mom = {T(0), T(0)};
         th.kin = {T(0), T(0)};
-        process_segment<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, th, a.err + r);
+        if (bulk) {
+            if (!process_segment_bulk<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, th, a.err + r,
+                                                                  pp, &s_abort))
+                return;      // a copy did not arrive: the run's flag says so
+        } else {
+            process_segment<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, th, a.err + r);
+        }
         // every CTA has been scheduled by now: let the next pass launch early
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
         __syncthreads();
@@ -780,10 +1061,13 @@ __global__ void __launch_bounds__(1024) k_phi(const RunDev *runs, int n_runs, co
 // ---------------------------------------------------------------------------
 size_t solve_smem_bytes(int max_nx) { return (size_t)max_nx * 8; }
 
-size_t pass_smem_bytes(int prec, int max_nx, int mode) {
+size_t pass_smem_bytes(int prec, int max_nx, int mode, bool decorated, int tpb, int stages) {
     const size_t t2 = (prec == SWPIC_F64) ? 16 : 8;
     const size_t me = (mode == SWPIC_DEPOSIT_ATOMIC) ? ((prec == SWPIC_F64) ? 8 : 4) : 8;
-    const size_t push = (size_t)max_nx * t2 + (size_t)(max_nx + 1) * me;
+    const size_t tb = (size_t)max_nx * t2, mb = (size_t)(max_nx + 1) * me;
+    size_t push = tb + mb;
+    if (stages >= 2)
+        push = stage_area_offset(tb, mb, tpb / 32, stages) + (size_t)stages * (decorated ? 5 : 3) * (size_t)tpb * 16;
     const size_t solve = solve_smem_bytes(max_nx);
     return push > solve ? push : solve;
 }

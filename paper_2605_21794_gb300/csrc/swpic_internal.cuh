@@ -22,6 +22,7 @@ constexpr int kDiagWords = 8;        // t, mass, momentum, kinetic, field, H, E_
 // error flags (bit mask in a device word)
 constexpr int kErrFixedOverflow = 1;
 constexpr int kErrNonFinite = 2;
+constexpr int kErrTimeout = 4;       // a bounded device wait ran out
 
 struct RunDev {
     int64_t p0, p1;          // particle range of the run
@@ -52,7 +53,7 @@ struct PassArgs {
     int32_t n_runs;
     int32_t d2_mode;
     int32_t max_nx;           // largest nx of the batch (shared-memory layout)
-    int32_t pad_;
+    int32_t stages;           // >= 2: bulk-copy pipeline with this many stages; else register loads
     const RunDev *runs;
     double c1, c2, cd;        // closing kick, opening kick, drift: fractions of dt
     uint32_t flags;
@@ -68,11 +69,11 @@ struct PassArgs {
     double *ring;             // [R][cap][kDiagWords]
     int32_t *ring_count;      // [R]
     int32_t ring_cap;
-    int32_t *err;             // [R] per-run anomaly flags (kErrFixedOverflow | kErrNonFinite)
+    int32_t *err;             // [R] per-run anomaly flags (kErr* bits)
 };
 
 // shared-memory bytes of the pass kernel / the per-run solve for a given max nx
-size_t pass_smem_bytes(int prec, int max_nx, int mode);
+size_t pass_smem_bytes(int prec, int max_nx, int mode, bool decorated, int tpb, int stages);
 size_t solve_smem_bytes(int max_nx);
 
 // launchers (return cudaError_t of the launch)

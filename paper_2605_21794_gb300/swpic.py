@@ -88,6 +88,8 @@ SIGNATURES = {
     "swpic_get_launch": (C.c_int, [_CTX, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
                                    C.POINTER(C.c_int32)]),
     "swpic_autotune": (C.c_int, [_CTX, C.c_int32, C.c_char_p]),
+    "swpic_set_pipeline": (C.c_int, [_CTX, C.c_int32]),
+    "swpic_get_pipeline": (C.c_int, [_CTX, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "swpic_set_timing": (C.c_int, [_CTX, C.c_int32]),
     "swpic_pass_times": (C.c_int, [_CTX, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
     "swpic_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
@@ -299,6 +301,17 @@ def swpic_autotune(ctx, steps_per_trial=5, cache_path=None):
                                          None if cache_path is None else cache_path.encode()), ctx)
 
 
+def swpic_set_pipeline(ctx, stages):
+    _check(load_library().swpic_set_pipeline(ctx, int(stages)), ctx)
+
+
+def swpic_get_pipeline(ctx):
+    """(requested, effective) bulk-copy stage counts; 0 = register loads."""
+    a, b = C.c_int32(), C.c_int32()
+    _check(load_library().swpic_get_pipeline(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
 def swpic_set_timing(ctx, enable):
     _check(load_library().swpic_set_timing(ctx, int(bool(enable))), ctx)
 
@@ -327,7 +340,8 @@ class Simulation:
 
     def __init__(self, runs, precision=32, decorated=True, deposit_mode=0, d2_mode=0,
                  resort_every=0, threads_per_block=0, blocks_per_sm=0, use_graphs=True,
-                 diag_capacity=0, with_scratch=True, stream=None, device="cuda"):
+                 diag_capacity=0, with_scratch=True, stream=None, device="cuda",
+                 pipeline_stages=None):
         import torch
         self.torch = torch
         self.precision = precision
@@ -342,6 +356,8 @@ class Simulation:
                             threads_per_block, blocks_per_sm, use_graphs, diag_capacity)
                 for (L, dt, nx, _) in self.runs]
         self.ctx = swpic_create_batch(cfgs, self.offsets)
+        if pipeline_stages is not None:
+            swpic_set_pipeline(self.ctx, pipeline_stages)
         n = max(self.n, 1)
         mk = lambda: torch.zeros(n, dtype=self.dtype, device=device)
         self.Q, self.P, self.psi = mk(), mk(), mk()
