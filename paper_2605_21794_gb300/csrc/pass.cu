@@ -48,12 +48,26 @@ template <> struct Vec16<double> { using type = double2; static constexpr int n 
 __device__ __forceinline__ float flo(float x) { return floorf(x); }
 __device__ __forceinline__ double flo(double x) { return floor(x); }
 
-template <typename T> struct Geo { T L, inv_h, inv_L, dt, inv_h_lo, L_lo; };
+// A value the compiler must keep (or spill) rather than re-derive: under
+// register pressure it would otherwise recompute loop-invariant values inside
+// the particle loop, and conversions and FP64 arithmetic run on a narrow pipe
+// on this GPU.
+__device__ __forceinline__ float opaque(float x) {
+    asm volatile("" : "+f"(x));
+    return x;
+}
+__device__ __forceinline__ double opaque(double x) {
+    asm volatile("" : "+d"(x));
+    return x;
+}
+
+// cmax = nx - 1/2 bounds the element coordinate (see elem_index)
+template <typename T> struct Geo { T L, inv_h, inv_L, dt, inv_h_lo, L_lo, cmax; };
 __device__ __forceinline__ Geo<float> geo_of(const RunDev &r, float) {
-    return {r.Lf, r.inv_hf, r.inv_Lf, r.dtf, r.inv_hf_lo, r.L_lo};
+    return {r.Lf, r.inv_hf, r.inv_Lf, r.dtf, r.inv_hf_lo, r.L_lo, opaque((float)r.nx - 0.5f)};
 }
 __device__ __forceinline__ Geo<double> geo_of(const RunDev &r, double) {
-    return {r.L, r.inv_h, r.inv_L, r.dt, 0.0, 0.0};
+    return {r.L, r.inv_h, r.inv_L, r.dt, 0.0, 0.0, opaque((double)r.nx - 0.5)};
 }
 
 // Position inside element i, xi = Q nx/L - i.  The element index itself is
@@ -61,19 +75,21 @@ __device__ __forceinline__ Geo<double> geo_of(const RunDev &r, double) {
 // with the rounding error of that product and the low part of nx/L added
 // back, so an FP32 state does not see the ~nx ulp bias of fl32(nx/L) near
 // Q = L (the error of xi stays at the ulp of xi, not of Q nx/L).
-__device__ __forceinline__ float xi_of(float Q, int i, const Geo<float> &G) {
-    const float p = Q * G.inv_h;
+// p = fl(Q inv_h) is the rounded product the element was decided from, fi the
+// element index as a float.
+__device__ __forceinline__ float xi_of(float Q, float p, float fi, const Geo<float> &G) {
     const float err = fmaf(Q, G.inv_h, -p);      // exact rounding error of the product
-    return (p - (float)i) + fmaf(Q, G.inv_h_lo, err);
+    return (p - fi) + fmaf(Q, G.inv_h_lo, err);
 }
-__device__ __forceinline__ double xi_of(double Q, int i, const Geo<double> &G) {
-    return Q * G.inv_h - (double)i;
+__device__ __forceinline__ double xi_of(double, double p, double fi, const Geo<double> &) {
+    return p - fi;
 }
 
+// element of Q (see elem_index); p and fi are kept for xi_of
 template <typename T>
-__device__ __forceinline__ int elem_of(T Q, T inv_h, int nx) {
-    int i = (int)flo(Q * inv_h);
-    return max(0, min(nx - 1, i));
+__device__ __forceinline__ int elem_of(T Q, const Geo<T> &G, T &p, T &fi) {
+    p = Q * G.inv_h;
+    return elem_index_c(p, G.cmax, fi);
 }
 
 // Periodic wrap into [0, L); a value that rounds up to L maps to 0.
@@ -123,7 +139,7 @@ __device__ __forceinline__ unsigned long long to_fixed(double x, double scale, i
     if (!(fabs(y) < 4.0e18)) { atomicOr(err, kErrFixedOverflow); return 0ull; }
     return (unsigned long long)__double2ll_rn(y);
 }
-__device__ __forceinline__ unsigned long long to_fixed(float x, double scale, int32_t *err) {
+__device__ __forceinline__ unsigned long long to_fixed(float x, float scale, int32_t *err) {
     float y = x * (float)scale;   // exact: scale is a power of two
     if (!(fabsf(y) < 4.0e18f)) { atomicOr(err, kErrFixedOverflow); return 0ull; }
     return (unsigned long long)__float2ll_rn(y);
@@ -415,7 +431,7 @@ struct Thread {
 };
 
 template <typename T, int MODE>
-__device__ __forceinline__ void mesh_add(int key, T a0, T a1, void *mesh, double scale, int32_t *err) {
+__device__ __forceinline__ void mesh_add(int key, T a0, T a1, void *mesh, T scale, int32_t *err) {
     if (MODE == SWPIC_DEPOSIT_ATOMIC) {
         T *m = reinterpret_cast<T *>(mesh);
         atomicAdd(m + key, a0);
@@ -434,7 +450,7 @@ __device__ __forceinline__ void mesh_add(int key, T a0, T a1, void *mesh, double
 // disordered plasma) the shuffles are skipped and every lane adds its own
 // value.  key < 0 marks an empty slot.  All 32 lanes must call this.
 template <typename T, int MODE>
-__device__ __forceinline__ void warp_deposit(int key, T a0, T a1, void *mesh, double scale,
+__device__ __forceinline__ void warp_deposit(int key, T a0, T a1, void *mesh, T scale,
                                              int32_t *err) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -461,12 +477,13 @@ __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
                                          const typename Vec2<T>::type *tab, const int nx,
                                          const Geo<T> &G, const T k1, const T k2, const T kd,
                                          T &dm, T &dk, int &key, T &w0, T &w1) {
-    const int i = elem_of(Q, G.inv_h, nx);
+    T p0, f0;
+    const int i = elem_of(Q, G, p0, f0);
     const auto f = tab[i];
     T d2 = T(0);
     if (DEC) {
         if (D2 == SWPIC_D2_NODAL) {
-            const T xi = xi_of(Q, i, G);
+            const T xi = xi_of(Q, p0, f0, G);
             const T g1 = tab[i + 1 == nx ? 0 : i + 1].y;
             d2 = fma(xi, g1 - f.y, f.y);
         } else {
@@ -487,8 +504,9 @@ __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
     Q = drift_wrap(Q, P, kd, G);
     if (DEC) ps = fma(-kd, qs, ps);
     if (DEP) {
-        key = elem_of(Q, G.inv_h, nx);
-        const T xi = xi_of(Q, key, G);
+        T p1, f1;
+        key = elem_of(Q, G, p1, f1);
+        const T xi = xi_of(Q, p1, f1, G);
         if (DEC) {
             const T dq = ps * G.inv_h;
             w0 = fma(w, T(1) - xi, dq);
@@ -507,6 +525,15 @@ __device__ __forceinline__ int find_run(const RunDev *runs, int n_runs, int64_t 
         if (runs[mid].p0 <= idx) lo = mid; else hi = mid - 1;
     }
     return lo;
+}
+
+// Kick and drift coefficients of a pass for one run, c dt rounded once to T
+// (opaque: the FP64 products are not to be recomputed per particle).
+template <typename T>
+__device__ __forceinline__ void step_coefficients(const PassArgs &a, const RunDev &R, T &k1, T &k2, T &kd) {
+    k1 = opaque((T)(a.c1 * R.dt));
+    k2 = opaque((T)(a.c2 * R.dt));
+    kd = opaque((T)(a.cd * R.dt));
 }
 
 // Deposit slots of one 16-byte vector of particles: element and node weights.
@@ -552,7 +579,7 @@ __device__ __forceinline__ void push_vector(typename Vec16<T>::type &q, typename
 // vectors share an element, costs one shared atomic per segment of lanes),
 // later runs go to the mesh directly.  All lanes of the warp must call this.
 template <typename T, int MODE>
-__device__ __forceinline__ void deposit_vector(const VecOut<T> &o, void *s_mesh, double scale, int32_t *err) {
+__device__ __forceinline__ void deposit_vector(const VecOut<T> &o, void *s_mesh, T scale, int32_t *err) {
     constexpr int VW = Vec16<T>::n;
     const int k0 = o.key[0];
     T s0 = o.w0[0], s1 = o.w1[0];
@@ -590,8 +617,9 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
     constexpr int VW = Vec16<T>::n;
     const Geo<T> G = geo_of(R, T());
     const int nx = R.nx;
-    const T k1 = (T)(a.c1 * R.dt), k2 = (T)(a.c2 * R.dt), kd = (T)(a.cd * R.dt);
-    const double scale = R.fx_scale;
+    T k1, k2, kd;
+    step_coefficients(a, R, k1, k2, kd);
+    const T scale = opaque((T)R.fx_scale);      // a power of two: exact in either type
     const bool wpsi = (a.flags & PASS_WRITE_PSI) != 0;
     const T *Qi = reinterpret_cast<const T *>(a.Qi), *Pi = reinterpret_cast<const T *>(a.Pi);
     const T *qsi = reinterpret_cast<const T *>(a.qsi), *psi = reinterpret_cast<const T *>(a.psi_i);
@@ -763,8 +791,9 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
     const unsigned full = 0xffffffffu;
     const Geo<T> G = geo_of(R, T());
     const int nx = R.nx;
-    const T k1 = (T)(a.c1 * R.dt), k2 = (T)(a.c2 * R.dt), kd = (T)(a.cd * R.dt);
-    const double scale = R.fx_scale;
+    T k1, k2, kd;
+    step_coefficients(a, R, k1, k2, kd);
+    const T scale = opaque((T)R.fx_scale);      // a power of two: exact in either type
     const bool wpsi = (a.flags & PASS_WRITE_PSI) != 0;
     const T *Qi = reinterpret_cast<const T *>(a.Qi), *Pi = reinterpret_cast<const T *>(a.Pi);
     const T *qsi = reinterpret_cast<const T *>(a.qsi), *psi = reinterpret_cast<const T *>(a.psi_i);
@@ -973,7 +1002,7 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
                 const int node = (j == nx) ? 0 : j;
                 if (MODE == SWPIC_DEPOSIT_ATOMIC) {
                     const T v = reinterpret_cast<T *>(s_mesh)[j];
-                    if (v != T(0)) atomicAdd(gacc + node, to_fixed(v, R.fx_scale, a.err + r));
+                    if (v != T(0)) atomicAdd(gacc + node, to_fixed(v, (T)R.fx_scale, a.err + r));
                 } else {
                     const unsigned long long v = reinterpret_cast<unsigned long long *>(s_mesh)[j];
                     if (v != 0ull) atomicAdd(gacc + node, v);

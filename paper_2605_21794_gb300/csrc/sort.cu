@@ -17,15 +17,13 @@
 
 namespace swpic {
 
-__device__ __forceinline__ float flo_s(float x) { return floorf(x); }
-__device__ __forceinline__ double flo_s(double x) { return floor(x); }
 __device__ __forceinline__ float inv_h_of(const RunDev &r, float) { return r.inv_hf; }
 __device__ __forceinline__ double inv_h_of(const RunDev &r, double) { return r.inv_h; }
 
 template <typename T>
 __device__ __forceinline__ int key_of(T Q, const RunDev &R) {
-    int i = (int)flo_s(Q * inv_h_of(R, T()));
-    return max(0, min(R.nx - 1, i));
+    T fi;
+    return elem_index(Q * inv_h_of(R, T()), R.nx, fi);
 }
 
 __device__ __forceinline__ int find_run_s(const RunDev *runs, int n_runs, int64_t idx) {

@@ -23,7 +23,7 @@
 #include <cmath>
 #include <mutex>
 
-#include "swpic.h"
+#include "swpic_internal.cuh"
 
 namespace {
 
@@ -66,17 +66,14 @@ __global__ void k_static_bound(const T *ps, const T *psi, int64_t n, double *bou
     }
 }
 
-__device__ __forceinline__ float floor_t(float x) { return floorf(x); }
-__device__ __forceinline__ double floor_t(double x) { return floor(x); }
-
-// position inside element i; in FP32 the rounding error of q*inv_h and the low
-// part of nx/L are added back so xi is accurate to its own ulp
-__device__ __forceinline__ float xi_t(float q, int i, float inv_h, float inv_h_lo) {
-    const float p = q * inv_h;
-    return (p - (float)i) + fmaf(q, inv_h_lo, fmaf(q, inv_h, -p));
+// position inside the element whose index fi was decided from p = fl(q inv_h);
+// in FP32 the rounding error of that product and the low part of nx/L are
+// added back so xi is accurate to its own ulp
+__device__ __forceinline__ float xi_t(float q, float p, float fi, float inv_h, float inv_h_lo) {
+    return (p - fi) + fmaf(q, inv_h_lo, fmaf(q, inv_h, -p));
 }
-__device__ __forceinline__ double xi_t(double q, int i, double inv_h, double) {
-    return q * inv_h - (double)i;
+__device__ __forceinline__ double xi_t(double, double p, double fi, double, double) {
+    return p - fi;
 }
 
 __device__ __forceinline__ double fixed_scale(const double *bound, double inv_h) {
@@ -97,9 +94,10 @@ __global__ void k_static_deposit(const T *Q, const T *ps, const T *psi, int64_t 
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
         const T q = Q[k];
-        int i = (int)floor_t(q * inv_h);
-        i = max(0, min(nx - 1, i));
-        const T xi = xi_t(q, i, inv_h, inv_h_lo);
+        const T p = q * inv_h;
+        T fi;
+        const int i = swpic::elem_index(p, nx, fi);
+        const T xi = xi_t(q, p, fi, inv_h, inv_h_lo);
         T w0 = psi[k] * (T(1) - xi), w1 = psi[k] * xi;
         if (ps) {
             const T dq = ps[k] * inv_h;

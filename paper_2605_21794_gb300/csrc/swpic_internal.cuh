@@ -24,6 +24,32 @@ constexpr int kErrFixedOverflow = 1;
 constexpr int kErrNonFinite = 2;
 constexpr int kErrTimeout = 4;       // a bounded device wait ran out
 
+// Element of a position: clamp(floor(p), 0, nx - 1) of the rounded product
+// p = fl(Q * nx/L), the definition shared by the pass, the sort keys and the
+// static deposit.  It is formed without float -> int conversions (which run on
+// the narrow FP64/conversion pipe of this GPU): after clamping p into
+// [0, nx - 1/2] (NaN -> 0), the sum 2^m + p rounded toward -inf is exactly
+// 2^m + floor(p) (m = 23 for float, 52 for double; p < nx <= 4096), so its bit
+// pattern minus that of 2^m is the index, and the sum minus 2^m is floor(p)
+// as a float (returned in fi).
+// cmax = nx - 1/2 (exact in either type).
+__device__ __forceinline__ int elem_index_c(float p, float cmax, float &fi) {
+    const float c = fminf(fmaxf(p, 0.0f), cmax);
+    const float y = __fadd_rd(c, 8388608.0f);
+    fi = y - 8388608.0f;
+    return __float_as_int(y) - 0x4B000000;
+}
+__device__ __forceinline__ int elem_index_c(double p, double cmax, double &fi) {
+    const double c = fmin(fmax(p, 0.0), cmax);
+    const double y = __dadd_rd(c, 4503599627370496.0);
+    fi = y - 4503599627370496.0;
+    return (int)(__double_as_longlong(y) - 0x4330000000000000ll);
+}
+template <typename T>
+__device__ __forceinline__ int elem_index(T p, int nx, T &fi) {
+    return elem_index_c(p, (T)nx - T(0.5), fi);
+}
+
 struct RunDev {
     int64_t p0, p1;          // particle range of the run
     double L, h, inv_h, dt;  // FP64 geometry; inv_h = nx / L
