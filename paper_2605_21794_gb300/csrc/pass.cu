@@ -119,11 +119,12 @@ __device__ __forceinline__ bool inside_f32(float Q, const Geo<float> &G) {
     return Q >= 0.0f && (Q - G.L) < G.L_lo;        // Q - L_hi is exact near L
 }
 __device__ __forceinline__ float drift_wrap(float Q, float P, float kd, const Geo<float> &G) {
-    float Qn = fmaf(kd, P, Q);
-    if (inside_f32(Qn, G) || Qn != Qn) return Qn;
-    if (Qn >= 0.0f) Qn = fmaf(kd, P, Q - G.L) - G.L_lo;   // crossed L
-    else Qn = (Qn + G.L) + G.L_lo;                          // crossed 0
-    if (inside_f32(Qn, G)) return Qn;
+    const float q0 = fmaf(kd, P, Q);
+    const float qa = fmaf(kd, P, Q - G.L) - G.L_lo;        // if it crossed L
+    const float qb = (q0 + G.L) + G.L_lo;                   // if it crossed 0
+    const bool in0 = inside_f32(q0, G) || q0 != q0;
+    float Qn = in0 ? q0 : (q0 >= 0.0f ? qa : qb);           // selects, no divergent branch
+    if (in0 || inside_f32(Qn, G)) return Qn;
     // several periods in one step, or a value that rounded onto the boundary
     const float k = floorf(Qn * G.inv_L);
     Qn = fmaf(-k, G.L_lo, fmaf(-k, G.L, Qn));
