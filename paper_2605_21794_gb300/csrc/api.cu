@@ -55,7 +55,7 @@ struct swpic_ctx {
     RunDev *d_runs = nullptr;
     std::vector<RunDev> h_runs;
     unsigned long long *d_acc = nullptr, *d_done = nullptr;
-    long long *d_snap = nullptr;
+    long long *d_snap = nullptr, *d_gauge = nullptr;
     void *d_table = nullptr;
     double *d_b = nullptr, *d_bt = nullptr, *d_e = nullptr, *d_phi = nullptr;
     double *d_diag_acc = nullptr, *d_field_diag = nullptr, *d_mass = nullptr, *d_mabs = nullptr;
@@ -160,7 +160,7 @@ void free_all(swpic_ctx *ctx) {
     ctx->graph_cache.clear();
     for (auto ev : ctx->events) cudaEventDestroy(ev);
     ctx->events.clear();
-    void *ptrs[] = {ctx->d_runs, ctx->d_acc, ctx->d_snap, ctx->d_done, ctx->d_table, ctx->d_b, ctx->d_bt, ctx->d_e,
+    void *ptrs[] = {ctx->d_runs, ctx->d_acc, ctx->d_snap, ctx->d_gauge, ctx->d_done, ctx->d_table, ctx->d_b, ctx->d_bt, ctx->d_e,
                     ctx->d_phi, ctx->d_diag_acc, ctx->d_field_diag, ctx->d_mass, ctx->d_mabs,
                     ctx->d_steps, ctx->d_ring, ctx->d_ring_count, ctx->d_err, ctx->d_chunks,
                     ctx->d_cnt, ctx->d_pos, ctx->d_scan_tmp, ctx->d_partials};
@@ -185,6 +185,7 @@ PassArgs base_args(swpic_ctx *ctx) {
     a.runs = ctx->d_runs;
     a.acc = ctx->d_acc;
     a.snap = ctx->d_snap;
+    a.gauge = ctx->d_gauge;
     a.table = ctx->d_table;
     a.b = ctx->d_b; a.btilde = ctx->d_bt; a.efield = ctx->d_e;
     a.run_done = ctx->d_done;
@@ -383,6 +384,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
         d.nx = c.nx;
         d.h = c.L / c.nx;
         d.inv_h = (double)c.nx / c.L;
+        d.inv_nx = 1.0 / (double)c.nx;
         d.inv_L = 1.0 / c.L;
         d.dt = c.dt;
         d.Lf = (float)c.L;
@@ -428,6 +430,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
     ok &= alloc((void **)&ctx->d_runs, sizeof(RunDev) * R);
     ok &= alloc((void **)&ctx->d_acc, sizeof(unsigned long long) * mo);
     ok &= alloc((void **)&ctx->d_snap, sizeof(long long) * mo);
+    ok &= alloc((void **)&ctx->d_gauge, sizeof(long long) * R);
     ok &= alloc((void **)&ctx->d_done, sizeof(unsigned long long) * R);
     ok &= alloc(&ctx->d_table, (size_t)mo * 2 * es);
     ok &= alloc((void **)&ctx->d_b, sizeof(double) * mo);
@@ -458,6 +461,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
     cudaMemset(ctx->d_err, 0, sizeof(int32_t) * R);
     cudaMemset(ctx->d_acc, 0, sizeof(unsigned long long) * mo);
     cudaMemset(ctx->d_snap, 0, sizeof(long long) * mo);
+    cudaMemset(ctx->d_gauge, 0, sizeof(long long) * R);
     cudaMemset(ctx->d_done, 0, sizeof(unsigned long long) * R);
     cudaMemset(ctx->d_steps, 0, sizeof(long long) * R);
     cudaMemset(ctx->d_ring_count, 0, sizeof(int32_t) * R);

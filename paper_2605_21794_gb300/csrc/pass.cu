@@ -219,31 +219,93 @@ __device__ __forceinline__ __int128 warp_sum_i128(__int128 v) {
     return v;
 }
 
+// Inputs of a run's diagnostic record, loaded by thread 0 into registers
+// before the solve (their latency overlaps it); the record is written after
+// the solve, with the field energy of the field this pass used (field_diag
+// before the solve overwrites it).
+struct DiagPre {
+    long long step;
+    int32_t count;
+    double mass, mom, kin, W, Ea;
+};
+__device__ __forceinline__ void diag_preload(const PassArgs &a, int r, DiagPre &d) {
+    d.step = a.steps[r];
+    d.count = a.ring_count[r];
+    d.mass = a.mass[r];
+    d.mom = __ldcg(a.diag_acc + 2 * r);
+    d.kin = __ldcg(a.diag_acc + 2 * r + 1);
+    d.W = a.field_diag[2 * r];
+    d.Ea = a.field_diag[2 * r + 1];
+}
+__device__ __forceinline__ void diag_write(const PassArgs &a, const RunDev &R, int r, const DiagPre &d) {
+    double *rec = a.ring + ((size_t)r * a.ring_cap + (size_t)(d.count % a.ring_cap)) * kDiagWords;
+    rec[0] = (double)d.step * R.dt;
+    rec[1] = d.mass;
+    rec[2] = d.mom;
+    rec[3] = d.kin;
+    rec[4] = d.W;
+    rec[5] = d.kin + d.W;
+    rec[6] = d.Ea;
+    rec[7] = (double)d.step;
+    a.ring_count[r] = d.count + 1;
+    a.diag_acc[2 * r] = 0.0;
+    a.diag_acc[2 * r + 1] = 0.0;
+}
+
+__device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
+    const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)v, o);
+    const unsigned long long hi = __shfl_xor_sync(0xffffffffu, (unsigned long long)(v >> 64), o);
+    return (__int128)(((unsigned __int128)hi << 64) | (unsigned __int128)lo);
+}
+__device__ __forceinline__ double i128_to_double(__int128 v) {
+    return (double)(long long)(v >> 64) * 18446744073709551616.0 + (double)(unsigned long long)v;
+}
+// nearest float to a 64-bit integer (ties to even, as a conversion rounds),
+// from integer operations only: the conversion instruction runs on the
+// narrow FP64/conversion pipe of this GPU
+__device__ __forceinline__ float ll_to_float(long long x) {
+    const unsigned long long ax = x < 0 ? 0ull - (unsigned long long)x : (unsigned long long)x;
+    if (ax == 0ull) return 0.0f;
+    const int lz = __clzll((long long)ax);
+    const unsigned long long m = ax << lz;                      // leading one at bit 63
+    unsigned mant = (unsigned)(m >> 40);                        // 24 bits with the leading one
+    const unsigned long long rest = m & 0xFFFFFFFFFFull, half = 0x8000000000ull;
+    mant += (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
+    const unsigned bits = ((unsigned)(190 - lz) << 23) + (mant - 0x800000u);   // a carry lifts the exponent
+    return __uint_as_float(bits | (x < 0 ? 0x80000000u : 0u));
+}
+
+// One CTA.  full = false: snapshot only (swpic_deposit's read-out).
 template <typename T>
 __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned char *smem, bool full) {
     using T2 = typename Vec2<T>::type;
-    __shared__ long long sh_ll[33];
-    __shared__ __int128 sh_q[32];
+    __shared__ long long sh_ll[34];
+    __shared__ __int128 sh_q[2][32];
     const int nx = R.nx, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    long long *s_p = reinterpret_cast<long long *>(smem);      // raw prefix P_j
+    long long *s_p = reinterpret_cast<long long *>(smem);      // raw acc, then e_int
     unsigned long long *acc = a.acc + R.mesh_off;
     long long *snap = a.snap + R.mesh_off;
     const int off = R.mesh_off;
     const int per = (nx + nt - 1) / nt;
     const int j0 = min(nx, tid * per), j1 = min(nx, j0 + per);
+    const long long c = a.gauge[r];           // reference for the field energy: the last gauge mean
 
-    // 1. own contiguous chunk: load, snapshot, clear, and its raw sum
-    long long tot = 0;
-    for (int j = j0; j < j1; ++j) {
+    // 1. load (coalesced; a thread's loads are independent and unrolled, so
+    //    the L2 round trips overlap), snapshot, clear
+#pragma unroll 8
+    for (int j = tid; j < nx; j += nt) {
         const long long v = (long long)__ldcg(acc + j);
         s_p[j] = v;
         snap[j] = v;
         if (full) acc[j] = 0ull;
-        tot += v;
     }
     if (!full) return;
-    // 2. one block scan of the raw accumulator gives the total S and P_j
+    __syncthreads();
+    // 2. one block scan of the chunk sums gives S = q nx + rem (0 <= rem < nx)
+    //    and the exclusive prefix P of this thread's chunk
+    long long tot = 0;
+    for (int j = j0; j < j1; ++j) tot += s_p[j];
     long long inc = tot;
     for (int o = 1; o < 32; o <<= 1) {
         const long long y = __shfl_up_sync(0xffffffffu, inc, o);
@@ -258,122 +320,100 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
             if (lane >= o) x += y;
         }
         if (lane < nw) sh_ll[lane] = x;                          // inclusive warp totals
-        if (lane == nw - 1) sh_ll[32] = x;                       // S
+        if (lane == nw - 1) {
+            long long qq = x / nx, rr = x % nx;
+            if (rr < 0) { rr += nx; qq -= 1; }
+            sh_ll[32] = qq;
+            sh_ll[33] = rr;
+        }
     }
     __syncthreads();
-    const long long S = sh_ll[32];
-    long long q = S / nx, rem = S % nx;                          // S = q nx + rem, 0 <= rem < nx
-    if (rem < 0) { rem += nx; q -= 1; }
-    long long P = ((warp > 0) ? sh_ll[warp - 1] : 0) + inc - tot; // exclusive prefix of my chunk
-    // e_int_j = P_j - (j+1) q  (exact Gauss prefix of btilde_j = acc_j - q), in place
-    __int128 es = 0;
+    const long long q = sh_ll[32], rem = sh_ll[33];
+    long long P = ((warp > 0) ? sh_ll[warp - 1] : 0) + inc - tot;
+    // 3. e_int_j = P_j - (j+1) q (exact Gauss prefix of btilde_j = acc_j - q),
+    //    with the exact sums of e_int and of ((e_int - c) >> 8)^2 for the gauge
+    //    and the field energy (one int128 block reduction for both)
+    __int128 es = 0, e2 = 0;
     for (int j = j0; j < j1; ++j) {
         P += s_p[j];
         const long long e = P - (long long)(j + 1) * q;
         s_p[j] = e;
         es += (__int128)e;
+        const long long e8 = (e - c) >> 8;                      // squares of 2^55 sum safely in int128
+        e2 += (__int128)e8 * e8;
     }
-    // 3. gauge: mean of e_int (int128 block sum; its barrier also publishes s_p)
-    {
-        const unsigned long long lo = (unsigned long long)es, hi = (unsigned long long)(es >> 64);
-        unsigned long long l2 = lo, h2 = hi;
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ol = __shfl_xor_sync(0xffffffffu, l2, o);
-            const unsigned long long oh = __shfl_xor_sync(0xffffffffu, h2, o);
-            const __int128 t = (__int128)(((unsigned __int128)h2 << 64) | l2) +
-                               (__int128)(((unsigned __int128)oh << 64) | ol);
-            l2 = (unsigned long long)t;
-            h2 = (unsigned long long)(t >> 64);
-        }
-        if (lane == 0) sh_q[warp] = (__int128)(((unsigned __int128)h2 << 64) | l2);
-        (void)lo; (void)hi;
+    for (int o = 16; o > 0; o >>= 1) {
+        es += shfl_xor_i128(es, o);
+        e2 += shfl_xor_i128(e2, o);
     }
+    __syncthreads();                                            // sh_ll reads above are done
+    if (lane == 0) { sh_q[0][warp] = es; sh_q[1][warp] = e2; }
     __syncthreads();
-    // mean = esum / nx as an integer part and a fraction, by thread 0 (the
-    // int128 -> double estimate is refined with exact integer arithmetic)
+    const double inv = R.fx_inv;
+    // 4. thread 0: gauge mean m = esum / nx (an integer part refined exactly
+    //    from a double estimate, and a fraction), field energy about the
+    //    reference, sum (e - m)^2 = sum (e - c)^2 - nx (m - c)^2 (no
+    //    cancellation while c is near m), W = (h/2) sum e^2 2^-2k, E_amp.
+    //    No FP64 division or square root in the FP32 path: they are long
+    //    serial sequences on this GPU's narrow FP64 pipe.
     if (tid == 0) {
-        __int128 esum = 0;
-        for (int w = 0; w < nw; ++w) esum += sh_q[w];
-        const double est = ((double)(long long)(esum >> 64) * 18446744073709551616.0 +
-                            (double)(unsigned long long)esum) / (double)nx;
-        long long mi = (long long)floor(est);
+        __int128 esum = 0, e2sum = 0;
+        for (int w = 0; w < nw; ++w) { esum += sh_q[0][w]; e2sum += sh_q[1][w]; }
+        long long mi = (long long)floor(i128_to_double(esum) * R.inv_nx);
         __int128 rr = esum - (__int128)mi * nx;
         while (rr < 0) { rr += nx; --mi; }
         while (rr >= nx) { rr -= nx; ++mi; }
         sh_ll[0] = mi;
         sh_ll[1] = (long long)rr;
+        const double d8 = ((double)(mi - c) + (double)rr * R.inv_nx) * (1.0 / 256.0);
+        const double sc = inv * 256.0;                          // undo the >> 8
+        double E2 = (i128_to_double(e2sum) - (double)nx * d8 * d8) * sc * sc;
+        if (E2 < 0.0) E2 = 0.0;
+        const double W = 0.5 * R.h * E2;
+        double Ea;
+        if (sizeof(T) == 4) Ea = (double)sqrtf((float)(E2 * R.inv_nx));   // FP32 state: FP32 precision
+        else Ea = sqrt(E2 * R.inv_nx);
+        a.field_diag[2 * r] = W;
+        a.field_diag[2 * r + 1] = Ea;
+        a.gauge[r] = mi;
+        if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
     }
     __syncthreads();
     const long long mean_i = sh_ll[0];
-    const double mfrac = (double)sh_ll[1] / (double)nx;
-    const double inv = R.fx_inv;
-    const double rem_node = (double)rem * inv / (double)nx;
-    const double cen = 0.5 * (double)(nx + 1);
+    // 5. the (phi_h', phi_h'') table
     T2 *tab = reinterpret_cast<T2 *>(a.table) + off;
-    __int128 e2i = 0;        // FP32 path: exact sum of ((e_int - mean) >> 8)^2
-    double e2d = 0.0;        // FP64 path
-    for (int j = j0; j < j1; ++j) {
-        const int jm = (j == 0) ? nx - 1 : j - 1, jp = (j == nx - 1) ? 0 : j + 1;
-        const long long ej_i = s_p[j];
-        const long long em_i = s_p[jm];
-        const long long ep_i = s_p[jp];
-        const long long ei = ej_i - mean_i;
-        const long long btj = (j == 0) ? ej_i : ej_i - em_i;
-        T2 t;
-        if (sizeof(T) == 4) {
-            // FP32 table straight from the exact integers; the sub-quantum
-            // gauge/remainder terms (< nx quanta) are below FP32 resolution
-            const float finv = (float)inv;                   // power of two: exact
-            t.x = (T)(-((float)ei * finv));
-            if (a.d2_mode == SWPIC_D2_NODAL)
-                t.y = (T)(-(float)btj * finv * (float)R.inv_h);
-            else
-                t.y = (T)((float)(em_i - ep_i) * finv * (float)(0.5 * R.inv_h));
-            const long long e8 = ei >> 8;                    // squares of 2^51 sum safely in int128
-            e2i += (__int128)e8 * e8;
-        } else {
-            auto efield = [&](long long eint, int kk) {
-                return ((double)(eint - mean_i) - mfrac) * inv - ((double)(kk + 1) - cen) * rem_node;
-            };
-            const double ej = efield(ej_i, j);
-            t.x = (T)(-ej);
-            if (a.d2_mode == SWPIC_D2_NODAL)
-                t.y = (T)(-((double)btj * inv - rem_node) * R.inv_h);
-            else
-                t.y = (T)((efield(em_i, jm) - efield(ep_i, jp)) * (0.5 * R.inv_h));
-            e2d += ej * ej;
-        }
-        tab[j] = t;
-    }
-    // 4. W = (h/2) sum E^2, E_amp (thread 0)
-    double E2 = 0.0;
     if (sizeof(T) == 4) {
-        __int128 t = e2i;
-        for (int o = 16; o > 0; o >>= 1) {
-            const unsigned long long ol = __shfl_xor_sync(0xffffffffu, (unsigned long long)t, o);
-            const unsigned long long oh = __shfl_xor_sync(0xffffffffu, (unsigned long long)(t >> 64), o);
-            t += (__int128)(((unsigned __int128)oh << 64) | ol);
-        }
-        __syncthreads();                                     // sh_q reuse
-        if (lane == 0) sh_q[warp] = t;
-        __syncthreads();
-        if (tid == 0) {
-            __int128 u = 0;
-            for (int w = 0; w < nw; ++w) u += sh_q[w];
-            const double hi = (double)(long long)(u >> 64), lo = (double)(unsigned long long)u;
-            const double sc = inv * 256.0;                   // undo the >> 8
-            E2 = (hi * 18446744073709551616.0 + lo) * sc * sc;
+        // FP32 table straight from the exact integers; the sub-quantum
+        // gauge/remainder terms (< nx quanta) are below FP32 resolution
+        const float finv = opaque((float)inv);                  // power of two: exact
+        const float f_inv_h = opaque((float)R.inv_h), f_half_inv_h = opaque((float)(0.5 * R.inv_h));
+        for (int j = j0; j < j1; ++j) {
+            const int jm = (j == 0) ? nx - 1 : j - 1, jp = (j == nx - 1) ? 0 : j + 1;
+            const long long ej_i = s_p[j], em_i = s_p[jm], ep_i = s_p[jp];
+            const long long btj = (j == 0) ? ej_i : ej_i - em_i;
+            T2 t;
+            t.x = (T)(-(ll_to_float(ej_i - mean_i) * finv));
+            if (a.d2_mode == SWPIC_D2_NODAL) t.y = (T)(-ll_to_float(btj) * finv * f_inv_h);
+            else t.y = (T)(ll_to_float(em_i - ep_i) * finv * f_half_inv_h);
+            tab[j] = t;
         }
     } else {
-        __shared__ double sh_d[32];
-        E2 = block_sum_d(e2d, sh_d);
-    }
-    if (tid == 0) {
-        const double W = 0.5 * R.h * E2;
-        const double Ea = sqrt(E2 / (double)nx);
-        a.field_diag[2 * r] = W;
-        a.field_diag[2 * r + 1] = Ea;
-        if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
+        const double mfrac = (double)sh_ll[1] * R.inv_nx;
+        const double rem_node = (double)rem * inv * R.inv_nx;
+        const double cen = 0.5 * (double)(nx + 1);
+        auto efield = [&](long long eint, int kk) {
+            return ((double)(eint - mean_i) - mfrac) * inv - ((double)(kk + 1) - cen) * rem_node;
+        };
+        for (int j = j0; j < j1; ++j) {
+            const int jm = (j == 0) ? nx - 1 : j - 1, jp = (j == nx - 1) ? 0 : j + 1;
+            const long long ej_i = s_p[j], em_i = s_p[jm], ep_i = s_p[jp];
+            const long long btj = (j == 0) ? ej_i : ej_i - em_i;
+            T2 t;
+            t.x = (T)(-efield(ej_i, j));
+            if (a.d2_mode == SWPIC_D2_NODAL) t.y = (T)(-((double)btj * inv - rem_node) * R.inv_h);
+            else t.y = (T)((efield(em_i, jm) - efield(ep_i, jp)) * (0.5 * R.inv_h));
+            tab[j] = t;
+        }
     }
 }
 
@@ -905,27 +945,12 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
 template <typename T>
 __device__ void finish_run(const PassArgs &a, const RunDev &R, int r, unsigned char *smem) {
     const uint32_t fl = a.flags;
-    if ((fl & PASS_DIAG) && threadIdx.x == 0) {
-        const long long st = a.steps[r];
-        const int32_t cnt = a.ring_count[r];
-        double *rec = a.ring + ((size_t)r * a.ring_cap + (size_t)(cnt % a.ring_cap)) * kDiagWords;
-        const double mom = __ldcg(a.diag_acc + 2 * r), kin = __ldcg(a.diag_acc + 2 * r + 1);
-        const double W = a.field_diag[2 * r], Ea = a.field_diag[2 * r + 1];
-        rec[0] = (double)st * R.dt;
-        rec[1] = a.mass[r];
-        rec[2] = mom;
-        rec[3] = kin;
-        rec[4] = W;
-        rec[5] = kin + W;
-        rec[6] = Ea;
-        rec[7] = (double)st;
-        a.ring_count[r] = cnt + 1;
-        a.diag_acc[2 * r] = 0.0;
-        a.diag_acc[2 * r + 1] = 0.0;
-    }
-    __syncthreads();
+    const bool diag = (fl & PASS_DIAG) != 0;
+    DiagPre pre;
+    if (diag && threadIdx.x == 0) diag_preload(a, r, pre);
     if (fl & PASS_SOLVE) solve_run<T>(a, R, r, smem, true);
     if (threadIdx.x == 0) {
+        if (diag) diag_write(a, R, r, pre);
         if (fl & PASS_COUNT_STEP) a.steps[r] += 1;
         a.run_done[r] = 0ull;
     }

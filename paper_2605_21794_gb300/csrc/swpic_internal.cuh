@@ -54,6 +54,7 @@ struct RunDev {
     int64_t p0, p1;          // particle range of the run
     double L, h, inv_h, dt;  // FP64 geometry; inv_h = nx / L
     double inv_L;
+    double inv_nx;           // 1 / nx
     double fx_scale;         // fixed-point scale 2^k of the charge accumulator
     double fx_inv;           // 2^-k
     float Lf, inv_hf, inv_Lf, dtf;  // FP32 copies (rounded once from the FP64 values)
@@ -85,6 +86,7 @@ struct PassArgs {
     uint32_t flags;
     unsigned long long *acc;  // int64 bit patterns
     long long *snap;          // int64 snapshot of acc taken by the last solve (read-out)
+    long long *gauge;         // [R] integer gauge mean of the last solve (reference of the next)
     void *table;              // T2 per element
     double *b, *btilde, *efield;
     unsigned long long *run_done;
