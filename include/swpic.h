@@ -86,7 +86,7 @@ typedef struct swpic_config {
     int32_t d2_mode;           /* swpic_d2_mode                                  */
     int32_t resort_every;      /* stable sort by cell every K steps; 0 = never   */
     int32_t threads_per_block; /* 0 = default (256); 64..1024, multiple of 32    */
-    int32_t blocks_per_sm;     /* 0 = default (4)                                */
+    int32_t blocks_per_sm;     /* 0 = default (3 FP32, 2 FP64)                   */
     int32_t use_graphs;        /* 1 = capture swpic_step() in CUDA graphs        */
     int32_t diag_capacity;     /* diagnostic records kept per run (0 = 4096)     */
 } swpic_config;

@@ -358,7 +358,8 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
     ctx->d2 = c0.d2_mode;
     ctx->resort = c0.resort_every;
     ctx->tpb = c0.threads_per_block ? c0.threads_per_block : 256;
-    ctx->bpsm = c0.blocks_per_sm ? c0.blocks_per_sm : 4;
+    // defaults that fit the register use of the particle pass at 256 threads
+    ctx->bpsm = c0.blocks_per_sm ? c0.blocks_per_sm : (c0.precision == SWPIC_F64 ? 2 : 3);
     ctx->graphs = c0.use_graphs != 0;
     ctx->cap = c0.diag_capacity ? c0.diag_capacity : 4096;
     auto bail = [&](swpic_status s) { free_all(ctx); delete ctx; return s; };
@@ -1143,7 +1144,7 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     const int tpbs[] = {128, 256, 512};
-    const int bpsms[] = {1, 2, 4, 8};
+    const int bpsms[] = {1, 2, 3, 4, 6, 8};
     std::vector<int> rss = {0};
     if (ctx->scratch) { rss.push_back(5); rss.push_back(20); rss.push_back(50); }
     const int pipes[] = {0, kDefaultStages};

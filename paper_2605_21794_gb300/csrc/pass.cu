@@ -41,9 +41,14 @@ namespace swpic {
 template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
-template <typename T> struct Vec16;   // 16-byte vector of T
-template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
+// The vector of particles one thread handles per array: two particles (8 bytes
+// of FP32 state, 16 of FP64).  Two FP32 particles rather than four keep the
+// FP32 push within 80 registers, so 24 warps fit an SM.  Vector ranges start
+// on 16-byte boundaries (kAlignParticles) for the bulk copies.
+template <typename T> struct Vec16;
+template <> struct Vec16<float> { using type = float2; static constexpr int n = 2; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
+template <typename T> struct AlignOf { static constexpr int n = 16 / (int)sizeof(T); };
 
 __device__ __forceinline__ float flo(float x) { return floorf(x); }
 __device__ __forceinline__ double flo(double x) { return floor(x); }
@@ -669,7 +674,7 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
     T *qso = reinterpret_cast<T *>(a.qso), *pso = reinterpret_cast<T *>(a.pso);
     T *wo = reinterpret_cast<T *>(a.wo);
 
-    // unaligned head / tail (fewer than VW particles each): one particle per
+    // unaligned head / tail (less than 16 bytes of particles each): one particle per
     // thread, shared-memory atomics without aggregation
     auto scalar = [&](int64_t k) {
         T Q = Qi[k], P = Pi[k], w = wi[k];
@@ -685,8 +690,9 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
         if (DEP) mesh_add<T, MODE>(key, w0, w1, s_mesh, scale, err);
     };
 
-    const int64_t vs = (s + VW - 1) / VW * VW;
-    const int64_t ve = e / VW * VW;
+    constexpr int A = AlignOf<T>::n;
+    const int64_t vs = (s + A - 1) / A * A;
+    const int64_t ve = e / A * A;
     if (vs >= ve) {
         for (int64_t k = s + threadIdx.x; k < e; k += blockDim.x) scalar(k);
         return;
@@ -858,8 +864,9 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
         if (DEP) mesh_add<T, MODE>(key, w0, w1, s_mesh, scale, err);
     };
 
-    const int64_t vs = (s + VW - 1) / VW * VW;
-    const int64_t ve = e / VW * VW;
+    constexpr int A = AlignOf<T>::n;
+    const int64_t vs = (s + A - 1) / A * A;
+    const int64_t ve = e / A * A;
     if (vs >= ve) {
         for (int64_t k = s + threadIdx.x; k < e; k += blockDim.x) scalar(k);
         return true;
@@ -957,7 +964,7 @@ __device__ void finish_run(const PassArgs &a, const RunDev &R, int r, unsigned c
 }
 
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
-__global__ void __launch_bounds__(512) k_pass(PassArgs a) {
+__device__ __forceinline__ void pass_body(const PassArgs &a) {
     using T2 = typename Vec2<T>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ int s_last, s_abort;
@@ -969,7 +976,7 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
     {
         const size_t tb = (size_t)a.max_nx * sizeof(T2), mb = mesh_bytes<T, MODE>(a.max_nx);
         const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
-        constexpr size_t stage_bytes = (DEC ? 5 : 3) * kWarpTile * 16;
+        constexpr size_t stage_bytes = (DEC ? 5 : 3) * kWarpTile * sizeof(typename Vec16<T>::type);
         pp.S = a.stages;
         pp.seq = 0;
         pp.bar = reinterpret_cast<uint64_t *>(smem + bar_offset(tb, mb)) + (size_t)w * pp.S;
@@ -1069,6 +1076,26 @@ __global__ void __launch_bounds__(512) k_pass(PassArgs a) {
     }
 }
 
+// FP32 state: at most 80 registers, so 24 warps (e.g. 3 x 256 or 6 x 128
+// threads) fit an SM; FP64 state: the push needs the full 128 (<= 512 threads).
+template <bool DEC, int MODE, bool DEP, bool DIAG, int D2>
+__global__ void __maxnreg__(80) k_pass32(PassArgs a) {
+    pass_body<float, DEC, MODE, DEP, DIAG, D2>(a);
+}
+template <bool DEC, int MODE, bool DEP, bool DIAG, int D2>
+__global__ void __launch_bounds__(512) k_pass64(PassArgs a) {
+    pass_body<double, DEC, MODE, DEP, DIAG, D2>(a);
+}
+template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2> struct PassKernel;
+template <bool DEC, int MODE, bool DEP, bool DIAG, int D2>
+struct PassKernel<float, DEC, MODE, DEP, DIAG, D2> {
+    static constexpr auto fn = k_pass32<DEC, MODE, DEP, DIAG, D2>;
+};
+template <bool DEC, int MODE, bool DEP, bool DIAG, int D2>
+struct PassKernel<double, DEC, MODE, DEP, DIAG, D2> {
+    static constexpr auto fn = k_pass64<DEC, MODE, DEP, DIAG, D2>;
+};
+
 // solve every run (one CTA per run); used by swpic_solve_field / deposit read-out
 template <typename T>
 __global__ void __launch_bounds__(1024) k_solve_runs(PassArgs a, int full) {
@@ -1122,7 +1149,8 @@ size_t pass_smem_bytes(int prec, int max_nx, int mode, bool decorated, int tpb, 
     const size_t tb = (size_t)max_nx * t2, mb = (size_t)(max_nx + 1) * me;
     size_t push = tb + mb;
     if (stages >= 2)
-        push = stage_area_offset(tb, mb, tpb / 32, stages) + (size_t)stages * (decorated ? 5 : 3) * (size_t)tpb * 16;
+        push = stage_area_offset(tb, mb, tpb / 32, stages) +
+               (size_t)stages * (decorated ? 5 : 3) * (size_t)tpb * (prec == SWPIC_F64 ? 16 : 8);
     const size_t solve = solve_smem_bytes(max_nx);
     return push > solve ? push : solve;
 }
@@ -1133,7 +1161,7 @@ static cudaError_t launch_pass_t(const PassArgs &a, int grid, int tpb, size_t sm
     const bool nodal = a.d2_mode == SWPIC_D2_NODAL;
 #define SWPIC_LAUNCH(DEP, DIAG, D2)                                                               \
     do {                                                                                          \
-        auto kern = k_pass<T, DEC, MODE, DEP, DIAG, D2>;                                          \
+        auto kern = PassKernel<T, DEC, MODE, DEP, DIAG, D2>::fn;                                  \
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                                (int)smem);                                        \
         if (err != cudaSuccess) return err;                                                       \
