@@ -65,6 +65,23 @@ def dist_env():
     return world, rank, local
 
 
+def job_time_ms(ms, world, device):
+    """The job's time over replicas: the slowest rank's (an all-reduce MAX of
+    one float on `device`; no collective when world == 1)."""
+    if world <= 1:
+        return float(ms)
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, particles_per_rank, steps, ms):
+    """Whole-job throughput: every rank advances its own replica of
+    particles_per_rank particles for `steps` steps within the job time."""
+    return world * particles_per_rank * steps / (ms / 1e3)
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -275,11 +292,8 @@ def main():
     clocks = sampler.stop() if sampler else None
     launches = swpic.swpic_launch_count(sim.ctx) - l0
     swpic.swpic_synchronize(sim.ctx)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n * args.steps / (ms / 1e3)
+    ms = job_time_ms(ms, world, "cuda")
+    value = job_value(world, n, args.steps, ms)
 
     # per-pass device durations (CUDA events on the context stream, plain launches),
     # over the same warm-up + K steps from the initial state
