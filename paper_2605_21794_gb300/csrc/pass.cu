@@ -655,6 +655,9 @@ __device__ __forceinline__ void deposit_vector(const VecOut<T> &o, void *s_mesh,
     warp_deposit<T, MODE>(k0, s0, s1, s_mesh, scale, err);
 }
 
+// vectors per array that one warp streams in one turn (both particle streams)
+constexpr int kWarpVecs = 64;
+
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
 __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, int64_t e,
                                 const typename Vec2<T>::type *s_tab, void *s_mesh, Thread<T> &th,
@@ -699,16 +702,18 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
     }
     for (int64_t k = s + threadIdx.x; k < vs; k += blockDim.x) scalar(k);
     const int64_t v0 = vs / VW, v1 = ve / VW;
-    constexpr int U = 2;
-    const int64_t stride = (int64_t)blockDim.x;
-    // warp-uniform trip count: every lane runs every iteration; out-of-range
-    // lanes carry empty deposit slots
-    for (int64_t vb = v0; vb < v1; vb += U * stride) {
+    constexpr int U = kWarpVecs / 32;
+    const int lane = threadIdx.x & 31;
+    const int64_t step = (int64_t)U * blockDim.x;                // vectors per CTA iteration
+    // warp w takes the kWarpVecs consecutive vectors v0 + k step + kWarpVecs w + [0, kWarpVecs)
+    // in its k-th turn, lane l the vectors l, 32 + l, ... of them; the trip count is
+    // warp-uniform and out-of-range lanes carry empty deposit slots
+    for (int64_t vb = v0 + (int64_t)U * (threadIdx.x - lane); vb < v1; vb += step) {
         V q[U], p[U], x[U], y[U], m[U];
         bool ok[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int64_t vv = vb + u * stride + threadIdx.x;
+            const int64_t vv = vb + 32 * u + lane;
             ok[u] = vv < v1;
             if (ok[u]) {
                 q[u] = reinterpret_cast<const V *>(Qi)[vv];
@@ -725,7 +730,7 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
             VecOut<T> o;
             if (ok[u]) {
                 push_vector<T, DEC, DEP, DIAG, D2>(q[u], p[u], x[u], y[u], m[u], s_tab, nx, G, k1, k2, kd, th, o);
-                const int64_t vv = vb + u * stride + threadIdx.x;
+                const int64_t vv = vb + 32 * u + lane;
                 reinterpret_cast<V *>(Qo)[vv] = q[u];
                 reinterpret_cast<V *>(Po)[vv] = p[u];
                 if (DEC) {
@@ -746,22 +751,23 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
 // Bulk-copy (TMA) staged particle stream
 // ---------------------------------------------------------------------------
 // Every warp streams its own particles: in its k-th turn warp w handles the
-// 32 vectors v0 + k blockDim.x + 32 w + [0, 32) of every array (the vectors
-// the register-load loop gives its lanes, in the same order).  Lane 0 copies
-// them global -> shared with cp.async.bulk (one copy of <= 512 B per array,
-// completion counted in bytes on the warp's mbarrier of that stage), S turns
-// ahead; as soon as the lanes have read a stage into registers (__syncwarp)
-// it is refilled with the turn S places further on, while the lanes push,
-// store (plain 16-byte stores) and deposit.  Warps never wait for each other,
-// so one warp's shared atomics overlap another's arithmetic, and the copy
-// engine keeps S x 32 x 16 B per array and warp in flight without registers.
+// kWarpVecs consecutive vectors v0 + k (kWarpVecs/32) blockDim.x + kWarpVecs w
+// + [0, kWarpVecs) of every array, lane l the vectors l, 32 + l, ... of them
+// (the vectors the register-load loop gives its lanes, in the same order).
+// Lane 0 copies them global -> shared with cp.async.bulk (one copy of at most
+// kWarpVecs vectors per array, completion counted in bytes on the warp's
+// mbarrier of that stage), S turns ahead; as soon as the lanes have read a
+// stage into registers (__syncwarp) it is refilled with the turn S places
+// further on, while the lanes push, store (plain stores) and deposit.  Warps
+// never wait for each other, so one warp's shared atomics overlap another's
+// arithmetic, and the copy engine keeps S turns per warp in flight without
+// holding registers.
 //
 // Every wait is bounded (kWaitLimitNs of wall time); a wait that runs out
 // sets kErrTimeout in the run's flag word, and the warp stops, waits (again
 // bounded) for its copies in flight, and the CTA leaves the kernel after the
 // segment.
 constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
-constexpr int kWarpTile = 32;        // vectors per array in one warp turn
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -821,7 +827,7 @@ __host__ __device__ __forceinline__ size_t stage_area_offset(size_t tab_bytes, s
 // Pipeline bookkeeping of one warp; seq counts the warp's turns over the CTA's
 // lifetime, so the stage of a turn is seq % S and its mbarrier parity (seq / S) & 1.
 struct Pipe {
-    unsigned char *base;     // this warp's S stages of n_arr x kWarpTile x 16 bytes
+    unsigned char *base;     // this warp's S stages of n_arr x kWarpVecs vectors
     uint64_t *bar;           // this warp's S mbarriers
     int S;
     uint32_t seq;
@@ -834,7 +840,7 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
     using V = typename Vec16<T>::type;
     constexpr int VW = Vec16<T>::n;
     constexpr int NA = DEC ? 5 : 3;                       // Q, P, w [, q*, p*]
-    constexpr uint32_t ARR = kWarpTile * sizeof(V);       // bytes per array in a stage
+    constexpr uint32_t ARR = kWarpVecs * sizeof(V);       // bytes per array in a stage
     const unsigned full = 0xffffffffu;
     const Geo<T> G = geo_of(R, T());
     const int nx = R.nx;
@@ -875,12 +881,13 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
 
     const int64_t v0 = vs / VW, v1 = ve / VW;
     const int lane = threadIdx.x & 31;
-    const int64_t wbase = v0 + (threadIdx.x - lane);       // first vector of this warp's turn 0
-    const int64_t stride = blockDim.x;
+    constexpr int U = kWarpVecs / 32;                      // vectors per lane and turn
+    const int64_t wbase = v0 + (int64_t)U * (threadIdx.x - lane);   // first vector of this warp's turn 0
+    const int64_t stride = (int64_t)U * blockDim.x;
     const int nturn = wbase < v1 ? (int)((v1 - wbase + stride - 1) / stride) : 0;
     const int S = pp.S;
 
-    auto turn_vecs = [&](int k) -> int { return (int)min((int64_t)kWarpTile, v1 - (wbase + (int64_t)k * stride)); };
+    auto turn_vecs = [&](int k) -> int { return (int)min((int64_t)kWarpVecs, v1 - (wbase + (int64_t)k * stride)); };
     auto issue = [&](int k) {            // lane 0 only
         const uint32_t q = pp.seq + (uint32_t)k;
         unsigned char *st = pp.base + (size_t)(q % S) * NA * ARR;
@@ -906,34 +913,44 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
             ok = false;
             break;
         }
-        const bool have = lane < turn_vecs(k);
-        V qv, pv, mv, xv, yv;
-        if (have) {
-            qv = sv[lane];
-            pv = sv[kWarpTile + lane];
-            mv = sv[2 * kWarpTile + lane];
-            if (DEC) { xv = sv[3 * kWarpTile + lane]; yv = sv[4 * kWarpTile + lane]; }
+        const int nv = turn_vecs(k);
+        bool have[U];
+        V qv[U], pv[U], mv[U], xv[U], yv[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int t = 32 * u + lane;
+            have[u] = t < nv;
+            if (have[u]) {
+                qv[u] = sv[t];
+                pv[u] = sv[kWarpVecs + t];
+                mv[u] = sv[2 * kWarpVecs + t];
+                if (DEC) { xv[u] = sv[3 * kWarpVecs + t]; yv[u] = sv[4 * kWarpVecs + t]; }
+            }
         }
         __syncwarp();                    // the stage has been read: refill it
         if (k + S < nturn) {
             if (lane == 0) issue(k + S);
             ++issued;
         }
-        VecOut<T> o;
-        if (have) {
-            push_vector<T, DEC, DEP, DIAG, D2>(qv, pv, xv, yv, mv, s_tab, nx, G, k1, k2, kd, th, o);
-            const int64_t vv = wbase + (int64_t)k * stride + lane;
-            reinterpret_cast<V *>(Qo)[vv] = qv;
-            reinterpret_cast<V *>(Po)[vv] = pv;
-            if (DEC) {
-                reinterpret_cast<V *>(qso)[vv] = xv;
-                reinterpret_cast<V *>(pso)[vv] = yv;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            VecOut<T> o;
+            if (have[u]) {
+                push_vector<T, DEC, DEP, DIAG, D2>(qv[u], pv[u], xv[u], yv[u], mv[u], s_tab, nx, G, k1, k2, kd,
+                                                   th, o);
+                const int64_t vv = wbase + (int64_t)k * stride + 32 * u + lane;
+                reinterpret_cast<V *>(Qo)[vv] = qv[u];
+                reinterpret_cast<V *>(Po)[vv] = pv[u];
+                if (DEC) {
+                    reinterpret_cast<V *>(qso)[vv] = xv[u];
+                    reinterpret_cast<V *>(pso)[vv] = yv[u];
+                }
+                if (wpsi) reinterpret_cast<V *>(wo)[vv] = mv[u];
+            } else {
+                o.clear();
             }
-            if (wpsi) reinterpret_cast<V *>(wo)[vv] = mv;
-        } else {
-            o.clear();
+            if (DEP) deposit_vector<T, MODE>(o, s_mesh, scale, err);
         }
-        if (DEP) deposit_vector<T, MODE>(o, s_mesh, scale, err);
     }
     if (!ok && lane == 0) {
         // drain: wait (bounded) for every copy still in flight into this warp's stages
@@ -976,7 +993,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
     {
         const size_t tb = (size_t)a.max_nx * sizeof(T2), mb = mesh_bytes<T, MODE>(a.max_nx);
         const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
-        constexpr size_t stage_bytes = (DEC ? 5 : 3) * kWarpTile * sizeof(typename Vec16<T>::type);
+        constexpr size_t stage_bytes = (DEC ? 5 : 3) * kWarpVecs * sizeof(typename Vec16<T>::type);
         pp.S = a.stages;
         pp.seq = 0;
         pp.bar = reinterpret_cast<uint64_t *>(smem + bar_offset(tb, mb)) + (size_t)w * pp.S;
@@ -1150,7 +1167,7 @@ size_t pass_smem_bytes(int prec, int max_nx, int mode, bool decorated, int tpb, 
     size_t push = tb + mb;
     if (stages >= 2)
         push = stage_area_offset(tb, mb, tpb / 32, stages) +
-               (size_t)stages * (decorated ? 5 : 3) * (size_t)tpb * (prec == SWPIC_F64 ? 16 : 8);
+               (size_t)stages * (decorated ? 5 : 3) * (size_t)(tpb / 32) * kWarpVecs * (prec == SWPIC_F64 ? 16 : 8);
     const size_t solve = solve_smem_bytes(max_nx);
     return push > solve ? push : solve;
 }
