@@ -655,8 +655,12 @@ __device__ __forceinline__ void deposit_vector(const VecOut<T> &o, void *s_mesh,
     warp_deposit<T, MODE>(k0, s0, s1, s_mesh, scale, err);
 }
 
-// vectors per array that one warp streams in one turn (both particle streams)
-constexpr int kWarpVecs = 64;
+// One warp turn (both particle streams) covers 512 bytes of every array:
+// 64 two-particle FP32 vectors or 32 FP64 vectors.
+constexpr int kTurnBytes = 512;
+template <typename T> struct TurnVecs {
+    static constexpr int n = kTurnBytes / (int)sizeof(typename Vec16<T>::type);
+};
 
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
 __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, int64_t e,
@@ -702,10 +706,10 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
     }
     for (int64_t k = s + threadIdx.x; k < vs; k += blockDim.x) scalar(k);
     const int64_t v0 = vs / VW, v1 = ve / VW;
-    constexpr int U = kWarpVecs / 32;
+    constexpr int U = TurnVecs<T>::n / 32;
     const int lane = threadIdx.x & 31;
     const int64_t step = (int64_t)U * blockDim.x;                // vectors per CTA iteration
-    // warp w takes the kWarpVecs consecutive vectors v0 + k step + kWarpVecs w + [0, kWarpVecs)
+    // warp w takes the N = TurnVecs<T>::n consecutive vectors v0 + k step + N w + [0, N)
     // in its k-th turn, lane l the vectors l, 32 + l, ... of them; the trip count is
     // warp-uniform and out-of-range lanes carry empty deposit slots
     for (int64_t vb = v0 + (int64_t)U * (threadIdx.x - lane); vb < v1; vb += step) {
@@ -751,11 +755,11 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
 // Bulk-copy (TMA) staged particle stream
 // ---------------------------------------------------------------------------
 // Every warp streams its own particles: in its k-th turn warp w handles the
-// kWarpVecs consecutive vectors v0 + k (kWarpVecs/32) blockDim.x + kWarpVecs w
-// + [0, kWarpVecs) of every array, lane l the vectors l, 32 + l, ... of them
+// N = TurnVecs<T>::n consecutive vectors v0 + k (N/32) blockDim.x + N w
+// + [0, N) of every array, lane l the vectors l, 32 + l, ... of them
 // (the vectors the register-load loop gives its lanes, in the same order).
 // Lane 0 copies them global -> shared with cp.async.bulk (one copy of at most
-// kWarpVecs vectors per array, completion counted in bytes on the warp's
+// N vectors per array, completion counted in bytes on the warp's
 // mbarrier of that stage), S turns ahead; as soon as the lanes have read a
 // stage into registers (__syncwarp) it is refilled with the turn S places
 // further on, while the lanes push, store (plain stores) and deposit.  Warps
@@ -827,7 +831,7 @@ __host__ __device__ __forceinline__ size_t stage_area_offset(size_t tab_bytes, s
 // Pipeline bookkeeping of one warp; seq counts the warp's turns over the CTA's
 // lifetime, so the stage of a turn is seq % S and its mbarrier parity (seq / S) & 1.
 struct Pipe {
-    unsigned char *base;     // this warp's S stages of n_arr x kWarpVecs vectors
+    unsigned char *base;     // this warp's S stages of n_arr x one turn (kTurnBytes per array)
     uint64_t *bar;           // this warp's S mbarriers
     int S;
     uint32_t seq;
@@ -840,7 +844,7 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
     using V = typename Vec16<T>::type;
     constexpr int VW = Vec16<T>::n;
     constexpr int NA = DEC ? 5 : 3;                       // Q, P, w [, q*, p*]
-    constexpr uint32_t ARR = kWarpVecs * sizeof(V);       // bytes per array in a stage
+    constexpr uint32_t ARR = TurnVecs<T>::n * sizeof(V);       // bytes per array in a stage
     const unsigned full = 0xffffffffu;
     const Geo<T> G = geo_of(R, T());
     const int nx = R.nx;
@@ -881,13 +885,13 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
 
     const int64_t v0 = vs / VW, v1 = ve / VW;
     const int lane = threadIdx.x & 31;
-    constexpr int U = kWarpVecs / 32;                      // vectors per lane and turn
+    constexpr int U = TurnVecs<T>::n / 32;                      // vectors per lane and turn
     const int64_t wbase = v0 + (int64_t)U * (threadIdx.x - lane);   // first vector of this warp's turn 0
     const int64_t stride = (int64_t)U * blockDim.x;
     const int nturn = wbase < v1 ? (int)((v1 - wbase + stride - 1) / stride) : 0;
     const int S = pp.S;
 
-    auto turn_vecs = [&](int k) -> int { return (int)min((int64_t)kWarpVecs, v1 - (wbase + (int64_t)k * stride)); };
+    auto turn_vecs = [&](int k) -> int { return (int)min((int64_t)TurnVecs<T>::n, v1 - (wbase + (int64_t)k * stride)); };
     auto issue = [&](int k) {            // lane 0 only
         const uint32_t q = pp.seq + (uint32_t)k;
         unsigned char *st = pp.base + (size_t)(q % S) * NA * ARR;
@@ -922,9 +926,9 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
             have[u] = t < nv;
             if (have[u]) {
                 qv[u] = sv[t];
-                pv[u] = sv[kWarpVecs + t];
-                mv[u] = sv[2 * kWarpVecs + t];
-                if (DEC) { xv[u] = sv[3 * kWarpVecs + t]; yv[u] = sv[4 * kWarpVecs + t]; }
+                pv[u] = sv[TurnVecs<T>::n + t];
+                mv[u] = sv[2 * TurnVecs<T>::n + t];
+                if (DEC) { xv[u] = sv[3 * TurnVecs<T>::n + t]; yv[u] = sv[4 * TurnVecs<T>::n + t]; }
             }
         }
         __syncwarp();                    // the stage has been read: refill it
@@ -993,7 +997,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
     {
         const size_t tb = (size_t)a.max_nx * sizeof(T2), mb = mesh_bytes<T, MODE>(a.max_nx);
         const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
-        constexpr size_t stage_bytes = (DEC ? 5 : 3) * kWarpVecs * sizeof(typename Vec16<T>::type);
+        constexpr size_t stage_bytes = (DEC ? 5 : 3) * TurnVecs<T>::n * sizeof(typename Vec16<T>::type);
         pp.S = a.stages;
         pp.seq = 0;
         pp.bar = reinterpret_cast<uint64_t *>(smem + bar_offset(tb, mb)) + (size_t)w * pp.S;
@@ -1167,7 +1171,7 @@ size_t pass_smem_bytes(int prec, int max_nx, int mode, bool decorated, int tpb, 
     size_t push = tb + mb;
     if (stages >= 2)
         push = stage_area_offset(tb, mb, tpb / 32, stages) +
-               (size_t)stages * (decorated ? 5 : 3) * (size_t)(tpb / 32) * kWarpVecs * (prec == SWPIC_F64 ? 16 : 8);
+               (size_t)stages * (decorated ? 5 : 3) * (size_t)(tpb / 32) * kTurnBytes;
     const size_t solve = solve_smem_bytes(max_nx);
     return push > solve ? push : solve;
 }
