@@ -257,9 +257,10 @@ def main():
         swpic.swpic_set_pipeline(sim.ctx, args.stages)
     fixed = args.launch is not None or args.stages is not None
     if args.resort < 0 and not args.no_autotune and not fixed:
-        # tune on the state the timed region sees (after the warm-up), then restart
-        sim.step(args.warmup, args.diag_every)
-        swpic.swpic_autotune(sim.ctx, 20, None)
+        # tune on a state like most of the timed region's (the lattice order is
+        # gone after ~300 steps), then restart from the initial state
+        sim.step(max(args.warmup, 300), args.diag_every)
+        swpic.swpic_autotune(sim.ctx, 30, None)
     tpb, bpsm, resort = swpic.swpic_get_launch(sim.ctx)
     stages = swpic.swpic_get_pipeline(sim.ctx)[1]
     restore(sim)

@@ -312,9 +312,10 @@ swpic_status swpic_set_pipeline(swpic_ctx *ctx, int32_t stages);
 swpic_status swpic_get_pipeline(const swpic_ctx *ctx, int32_t *requested, int32_t *effective);
 
 /* Times a small grid of launch shapes, particle-load pipelines and re-sort
- * intervals on the bound
- * state (which is saved before and restored after, bit for bit) and keeps
- * the fastest.  steps_per_trial > 0.  cache_path: JSON file read before and
+ * intervals on the bound state (which is saved before and restored after, bit
+ * for bit; trial steps record diagnostics every step) and keeps the fastest.
+ * Tune on a state like the one to be run: the fastest shape for a freshly
+ * initialised (ordered) lattice differs from the one for a mixed plasma.  steps_per_trial > 0.  cache_path: JSON file read before and
  * updated after tuning, keyed by (GPU, precision, decoration, deposit mode,
  * runs, particles, total mesh size); NULL = no cache.  Synchronous. */
 swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char *cache_path);

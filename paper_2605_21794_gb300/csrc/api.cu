@@ -1168,7 +1168,7 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
                         st = restore();
                         if (st != SWPIC_OK) break;
                         cudaEventRecord(e0, ctx->stream);
-                        st = swpic_step(ctx, n_trial, 0);
+                        st = swpic_step(ctx, n_trial, 1);      // steps with their diagnostics
                         cudaEventRecord(e1, ctx->stream);
                         if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, SWPIC_ECUDA, "autotune trial");
                         cudaEventElapsedTime(&ms, e0, e1);
