@@ -63,6 +63,14 @@ def lib():
         L.or_gauss_legendre.restype = C.c_int
         L.or_gauss_legendre.argtypes = [C.c_int32, _D, _D]
         L.or_init_lattice.restype = C.c_int
+        L.or_kmeans_assign.argtypes = [C.c_int64, _D, _D, C.c_int32, _D, _D, C.c_double, _I32]
+        L.or_kmeans_assign.restype = None
+        L.or_kmeans_means.argtypes = [C.c_int64, _D, _D, _D, _I32, C.c_int32, C.c_double, _D, _D, _D, _D, _D]
+        L.or_kmeans_means.restype = None
+        L.or_kmeans.argtypes = [C.c_int64, _D, _D, _D, C.c_int32, C.c_double, C.c_int32, _D, _D, _I32]
+        L.or_kmeans.restype = None
+        L.or_lump.argtypes = [C.c_int64, _D, _D, _D, _I32, C.c_int32, C.c_double, _D, _D, _D, _D, _D, _D, _D]
+        L.or_lump.restype = C.c_int64
         L.or_init_lattice.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.c_double, C.c_double, C.c_double, C.c_int32,
                                       _D, _D, _D, _D, _D, C.c_int32, C.c_int32, _D, _D,
@@ -281,3 +289,44 @@ def stable_sort_order(keys):
     (key, original index).  Definition of a stable counting sort."""
     keys = np.asarray(keys)
     return np.lexsort((np.arange(len(keys)), keys))
+
+
+# --- decorated-particle initialization from marker particles (Alg. lumping_procedure) ---
+def kmeans_assign(Qm, Pm, cq, cp, L):
+    """Nearest center of every marker (FP32 decision, ties to the smaller index)."""
+    Qm, Pm, cq, cp = _f64(Qm), _f64(Pm), _f64(cq), _f64(cp)
+    out = np.zeros(len(Qm), dtype=np.int32)
+    lib().or_kmeans_assign(len(Qm), _d(Qm), _d(Pm), len(cq), _d(cq), _d(cp), L, _i(out))
+    return out
+
+
+def kmeans_means(Qm, Pm, wm, assign, cq, cp, L):
+    """psi-weighted member means about the centers; (mq, mp, w_sum)."""
+    Qm, Pm, wm, cq, cp = _f64(Qm), _f64(Pm), _f64(wm), _f64(cq), _f64(cp)
+    assign = np.ascontiguousarray(assign, dtype=np.int32)
+    K = len(cq)
+    mq, mp, ws = np.zeros(K), np.zeros(K), np.zeros(K)
+    lib().or_kmeans_means(len(Qm), _d(Qm), _d(Pm), _d(wm), _i(assign), K, L, _d(cq), _d(cp),
+                          _d(mq), _d(mp), _d(ws))
+    return mq, mp, ws
+
+
+def kmeans(Qm, Pm, wm, cq0, cp0, L, n_iter):
+    """n_iter Lloyd iterations from (cq0, cp0); returns (cq, cp, assign)."""
+    Qm, Pm, wm = _f64(Qm), _f64(Pm), _f64(wm)
+    cq, cp = np.array(cq0, dtype=np.float64), np.array(cp0, dtype=np.float64)
+    assign = np.zeros(len(Qm), dtype=np.int32)
+    lib().or_kmeans(len(Qm), _d(Qm), _d(Pm), _d(wm), len(cq), L, int(n_iter), _d(cq), _d(cp), _i(assign))
+    return cq, cp, assign
+
+
+def lump(Qm, Pm, wm, assign, cq, cp, L):
+    """Alg. lumping_procedure: decorated particles of the non-empty clusters."""
+    Qm, Pm, wm, cq, cp = _f64(Qm), _f64(Pm), _f64(wm), _f64(cq), _f64(cp)
+    assign = np.ascontiguousarray(assign, dtype=np.int32)
+    K = len(cq)
+    out = [np.zeros(K) for _ in range(5)]
+    n = lib().or_lump(len(Qm), _d(Qm), _d(Pm), _d(wm), _i(assign), K, L, _d(cq), _d(cp),
+                      *[_d(a) for a in out])
+    Q, P, qs, ps, psi = [a[:n].copy() for a in out]
+    return {"Q": Q, "P": P, "qs": qs, "ps": ps, "psi": psi}

@@ -635,3 +635,138 @@ int or_init_lattice(int32_t nq, int32_t nv, double L, double vmin, double vmax,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Decorated-particle initialization from marker particles                   */
+/* (Sec. 4.1-4.2 "Initialization", Alg. lumping_procedure, Eqs. psi-star and */
+/* moment-def, with the periodic c of the T^d subsection).                   */
+/*                                                                           */
+/* Reading of "k-means on the phase-space coordinates" on the torus: Lloyd    */
+/* iterations in (q, p) with the minimum-image difference in q.  The         */
+/* assignment is a decision, taken in FP32 (the precision of the GPU path):  */
+/* dq = Qm - cq (floats, folded once into [-L/2, L/2)), dp = Pm - cp,         */
+/* d2 = dq*dq + dp*dp, ties to the smaller cluster index.  Centers are the   */
+/* psi-weighted member means in FP64, q unwrapped about the current center   */
+/* and wrapped into [0, L); an empty cluster keeps its center.               */
+/* ------------------------------------------------------------------------ */
+static float km_fold(float d, float L, float half) {
+    if (d >= half) return d - L;
+    if (d < -half) return d + L;
+    return d;
+}
+static double km_fold_d(double d, double L) {
+    if (d >= 0.5 * L) return d - L;
+    if (d < -0.5 * L) return d + L;
+    return d;
+}
+
+/* nearest center of every marker (FP32 decision) */
+void or_kmeans_assign(int64_t M, const double *Qm, const double *Pm, int32_t K,
+                      const double *cq, const double *cp, double L, int32_t *assign) {
+    const float Lf = (float)L, half = (float)(0.5 * L);
+    for (int64_t A = 0; A < M; ++A) {
+        const float qf = (float)Qm[A], pf = (float)Pm[A];
+        float best = INFINITY;
+        int32_t bi = 0;
+        for (int32_t k = 0; k < K; ++k) {
+            const float dq = km_fold(qf - (float)cq[k], Lf, half);
+            const float dp = pf - (float)cp[k];
+            const float d2 = dq * dq + dp * dp;
+            if (d2 < best) { best = d2; bi = k; }
+        }
+        assign[A] = bi;
+    }
+}
+
+/* psi-weighted member means about the given centers (FP64, marker order);
+   w_sum[k] = 0 leaves the center unchanged */
+void or_kmeans_means(int64_t M, const double *Qm, const double *Pm, const double *wm,
+                     const int32_t *assign, int32_t K, double L, const double *cq, const double *cp,
+                     double *mq, double *mp, double *w_sum) {
+    double *sq = (double *)calloc((size_t)K, sizeof(double));
+    double *sp = (double *)calloc((size_t)K, sizeof(double));
+    for (int32_t k = 0; k < K; ++k) w_sum[k] = 0.0;
+    for (int64_t A = 0; A < M; ++A) {
+        const int32_t k = assign[A];
+        w_sum[k] += wm[A];
+        sq[k] += wm[A] * km_fold_d(Qm[A] - cq[k], L);
+        sp[k] += wm[A] * Pm[A];
+    }
+    for (int32_t k = 0; k < K; ++k) {
+        if (w_sum[k] != 0.0) {
+            mq[k] = or_wrap(cq[k] + sq[k] / w_sum[k], L);
+            mp[k] = sp[k] / w_sum[k];
+        } else {
+            mq[k] = cq[k];
+            mp[k] = cp[k];
+        }
+    }
+    free(sq);
+    free(sp);
+}
+
+/* n_iter Lloyd iterations from the given centers (updated in place), then the
+   final assignment */
+void or_kmeans(int64_t M, const double *Qm, const double *Pm, const double *wm, int32_t K,
+               double L, int32_t n_iter, double *cq, double *cp, int32_t *assign) {
+    double *mq = (double *)malloc(sizeof(double) * (size_t)K);
+    double *mp = (double *)malloc(sizeof(double) * (size_t)K);
+    double *ws = (double *)malloc(sizeof(double) * (size_t)K);
+    for (int32_t it = 0; it < n_iter; ++it) {
+        or_kmeans_assign(M, Qm, Pm, K, cq, cp, L, assign);
+        or_kmeans_means(M, Qm, Pm, wm, assign, K, L, cq, cp, mq, mp, ws);
+        memcpy(cq, mq, sizeof(double) * (size_t)K);
+        memcpy(cp, mp, sizeof(double) * (size_t)K);
+    }
+    or_kmeans_assign(M, Qm, Pm, K, cq, cp, L, assign);
+    free(mq);
+    free(mp);
+    free(ws);
+}
+
+/* Alg. lumping_procedure for the clusters of `assign` (centers cq, cp: the q
+   unwrap reference of each cluster).  For every non-empty cluster, in cluster
+   order: psi* = sum psi (Eq. psi-star); (Q, P) = the member nearest (FP32
+   decision, ties to the smaller marker index) to the psi-weighted mean;
+   p* = sum psi (L/2pi) sin(2pi (Q - Qm)/L), q* = -sum psi (P - Pm)
+   (Eq. moment-def with the periodic c).  Returns the number of particles. */
+int64_t or_lump(int64_t M, const double *Qm, const double *Pm, const double *wm,
+                const int32_t *assign, int32_t K, double L, const double *cq, const double *cp,
+                double *Q, double *P, double *q_star, double *p_star, double *psi_star) {
+    const double pi = 3.14159265358979323846;
+    const float Lf = (float)L, half = (float)(0.5 * L);
+    double *mq = (double *)malloc(sizeof(double) * (size_t)K);
+    double *mp = (double *)malloc(sizeof(double) * (size_t)K);
+    double *ws = (double *)malloc(sizeof(double) * (size_t)K);
+    int64_t *a0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    float *best = (float *)malloc(sizeof(float) * (size_t)K);
+    or_kmeans_means(M, Qm, Pm, wm, assign, K, L, cq, cp, mq, mp, ws);
+    for (int32_t k = 0; k < K; ++k) { a0[k] = -1; best[k] = INFINITY; }
+    for (int64_t A = 0; A < M; ++A) {
+        const int32_t k = assign[A];
+        const float dq = km_fold((float)Qm[A] - (float)mq[k], Lf, half);
+        const float dp = (float)Pm[A] - (float)mp[k];
+        const float d2 = dq * dq + dp * dp;
+        if (a0[k] < 0 || d2 < best[k]) { best[k] = d2; a0[k] = A; }
+    }
+    /* compact index of each non-empty cluster */
+    int64_t n = 0;
+    int64_t *slot = (int64_t *)malloc(sizeof(int64_t) * (size_t)K);
+    for (int32_t k = 0; k < K; ++k) {
+        slot[k] = (a0[k] >= 0) ? n++ : -1;
+        if (slot[k] < 0) continue;
+        Q[slot[k]] = Qm[a0[k]];
+        P[slot[k]] = Pm[a0[k]];
+        psi_star[slot[k]] = 0.0;
+        p_star[slot[k]] = 0.0;
+        q_star[slot[k]] = 0.0;
+    }
+    for (int64_t A = 0; A < M; ++A) {
+        const int64_t s = slot[assign[A]];
+        psi_star[s] += wm[A];
+        p_star[s] += wm[A] * (L / (2.0 * pi)) * sin(2.0 * pi * (Q[s] - Qm[A]) / L);
+        q_star[s] += -wm[A] * (P[s] - Pm[A]);
+    }
+    free(mq); free(mp); free(ws); free(a0); free(best); free(slot);
+    return n;
+}
