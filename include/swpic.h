@@ -241,6 +241,35 @@ swpic_status swpic_synchronize(swpic_ctx *ctx);
  * must equal the runs. */
 swpic_status swpic_run_status(swpic_ctx *ctx, int32_t *flags, int32_t n_runs);
 
+/* ---- decorated particles from marker particles ---------------------------------- */
+
+/* Sec. 4.1-4.2 "Initialization" and Alg. lumping_procedure: k-means in phase
+ * space, then one decorated particle per non-empty cluster with
+ *   psi* = sum psi (Eq. psi-star),  (Q, P) = the member nearest to the cluster's
+ *   psi-weighted mean,  p* = sum psi (L/2pi) sin(2pi (Q - Qm)/L),
+ *   q* = -sum psi (P - Pm)  (Eq. moment-def with the periodic c).
+ * k-means: n_iter Lloyd iterations in (q, p), q differences by the minimum
+ * image; the nearest-center decision is taken in FP32 (ties to the smaller
+ * cluster index); centers move to the psi-weighted member means (q unwrapped
+ * about the current center, wrapped into [0, L)); an empty cluster keeps its
+ * center.  Member sums are exact (64-bit fixed point), so results do not
+ * depend on thread order except the FP64 atomic sums of p*, q*.
+ * All arrays are DEVICE memory, FP64 unless noted:
+ *   Qm, Pm, wm [M]   markers: positions in [0, L), momenta, weights (> 0);
+ *                    M < 2^32
+ *   cq, cp [K]       initial centers in, final centers out (K >= 1)
+ *   assign [M]       int32, final cluster of every marker; may be NULL
+ *   Q, P, qs, ps, psi [K]  the decorated particles of the non-empty clusters,
+ *                    in cluster order (Q, P, q*, p*, psi*)
+ *   n_out            HOST int64: number of decorated particles written
+ * Allocates its work buffers (stream-ordered) and frees them; synchronous.
+ * Errors: SWPIC_EINVAL for bad sizes/pointers, SWPIC_ENOMEM, SWPIC_ENUMERIC
+ * for non-finite weights or momenta, SWPIC_ECUDA. */
+swpic_status swpic_kmeans_lump(const double *Qm, const double *Pm, const double *wm, int64_t M,
+                               double *cq, double *cp, int32_t K, double L, int32_t n_iter,
+                               int32_t *assign, double *Q, double *P, double *qs, double *ps,
+                               double *psi, int64_t *n_out, swpic_stream stream);
+
 /* ---- deposit without device allocation ---------------------------------------- */
 
 /* Mesh charge b_j = sum_a psi*_a phi_j(Q_a) - p*_a phi_j'(Q_a) of one run, for
@@ -315,8 +344,8 @@ swpic_status swpic_get_pipeline(const swpic_ctx *ctx, int32_t *requested, int32_
  * intervals on the bound state (which is saved before and restored after, bit
  * for bit; trial steps record diagnostics every step) and keeps the fastest.
  * Tune on a state like the one to be run: the fastest shape for a freshly
- * initialised (ordered) lattice differs from the one for a mixed plasma.  steps_per_trial > 0.  cache_path: JSON file read before and
- * updated after tuning, keyed by (GPU, precision, decoration, deposit mode,
+ * initialised (ordered) lattice differs from the one for a mixed plasma.
+ * steps_per_trial > 0.  cache_path: JSON file read before and updated after tuning, keyed by (GPU, precision, decoration, deposit mode,
  * runs, particles, total mesh size); NULL = no cache.  Synchronous. */
 swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char *cache_path);
 

@@ -14,11 +14,12 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libswpic.so")
-SOURCES = ["api.cu", "pass.cu", "sort.cu", "init.cu", "static_deposit.cu"]
+SOURCES = ["api.cu", "pass.cu", "sort.cu", "init.cu", "kmeans.cu", "static_deposit.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
-# the particle pass writes its fused multiply-adds out; nothing else is contracted
-PER_SOURCE = {"pass.cu": ["-fmad=false"]}
+# the particle pass writes its fused multiply-adds out, and the k-means
+# assignment takes FP32 decisions from separately rounded operations
+PER_SOURCE = {"pass.cu": ["-fmad=false"], "kmeans.cu": ["-fmad=false"]}
 
 
 def _nvcc():

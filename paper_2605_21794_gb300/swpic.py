@@ -82,6 +82,8 @@ SIGNATURES = {
                                   C.c_int32, C.c_int32]),
     "swpic_deposit_static": (C.c_int, [_P, _P, _P, C.c_int64, C.c_int32, C.c_double, C.c_int32,
                                        _P, _P]),
+    "swpic_kmeans_lump": (C.c_int, [_P, _P, _P, C.c_int64, _P, _P, C.c_int32, C.c_double, C.c_int32,
+                                    _P, _P, _P, _P, _P, _P, C.POINTER(C.c_int64), _P]),
     "swpic_save": (C.c_int, [_CTX, C.c_char_p]),
     "swpic_load": (C.c_int, [_CTX, C.c_char_p]),
     "swpic_set_launch": (C.c_int, [_CTX, C.c_int32, C.c_int32, C.c_int32]),
@@ -275,6 +277,15 @@ def swpic_deposit_static(Q, ps, psi, n, precision, L, nx, b, stream):
     """Device pointers in/out (see include/swpic.h); allocates nothing."""
     _check(load_library().swpic_deposit_static(Q, ps, psi, int(n), int(precision), float(L),
                                                int(nx), b, stream))
+
+
+def swpic_kmeans_lump(Qm, Pm, wm, M, cq, cp, K, L, n_iter, assign, Q, P, qs, ps, psi, stream):
+    """Device pointers in/out (see include/swpic.h); returns the number of
+    decorated particles written."""
+    n = C.c_int64(0)
+    _check(load_library().swpic_kmeans_lump(Qm, Pm, wm, int(M), cq, cp, int(K), float(L), int(n_iter),
+                                            assign, Q, P, qs, ps, psi, C.byref(n), stream))
+    return n.value
 
 
 def swpic_save(ctx, path):

@@ -200,6 +200,26 @@ def random_state(n: int, L: float, seed: int = 0, vth: float = 1.0, decorated: b
     return {"Q": Q, "P": P, "qs": qs, "ps": ps, "psi": psi}
 
 
+def two_stream_markers(M: int, seed: int = 0, alpha: float = 0.01, L: float = 2 * np.pi,
+                       v0: float = 1.0, vth: float = 0.3) -> dict:
+    """A seeded random sample of M marker particles of the two-stream f0 of the
+    paper's initialization experiments: f0 ~ (1 + alpha cos(2 pi x / L)) x
+    (N(+v0, vth^2) + N(-v0, vth^2)) / 2 on [0, L).  x by rejection from
+    uniform proposals, v by Box-Muller; weights L / M.  FP64 arrays
+    (Q, P, psi)."""
+    n_prop = 2 * M + 64
+    u = uniform01(seed, 20, 5 * n_prop).reshape(5, n_prop)
+    xs = L * u[0]
+    keep = u[1] * (1.0 + abs(alpha)) <= 1.0 + alpha * np.cos(2 * np.pi * xs / L)
+    x = xs[keep][:M]
+    if len(x) < M:                                        # practically never: top up without rejection
+        x = np.concatenate([x, xs[~keep][:M - len(x)]])
+    r = np.sqrt(-2.0 * np.log(np.maximum(u[2][:M], 1e-300)))
+    g = r * np.cos(2 * np.pi * u[3][:M])
+    sign = np.where(u[4][:M] < 0.5, -1.0, 1.0)
+    return {"Q": x, "P": sign * v0 + vth * g, "psi": np.full(M, L / M)}
+
+
 def lattice_points(spec: LatticeSpec) -> Tuple[np.ndarray, np.ndarray]:
     """Cell centres (x_i, v_j) flattened x-major (index i * nv + j)."""
     dx = spec.L / spec.nq
