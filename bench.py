@@ -340,6 +340,7 @@ def main():
         restore(sim)
         line["e2e"] = e2e_leg(torch, swpic, sim, n, args)
         line["batched_vs_plain"] = ensemble_leg(torch, swpic)
+        line["init_kmeans"] = kmeans_leg(torch, swpic)
         line["cpu_baseline"] = cpu_baseline_leg(spec, args)
     elif rank == 0:
         restore(sim)
@@ -388,6 +389,42 @@ def e2e_leg(torch, swpic, sim, n, args):
             "h2d_bytes_per_step": 20 * n / args.steps, "d2h_bytes_per_step": 16 * n / args.steps,
             "note": "swpic_step_host: H2D of the 5 state arrays, field set-up, K steps, D2H of "
                     "(Q, P, q*, p*), all inside the timed region"}
+
+
+def kmeans_leg(torch, swpic):
+    """Decorated particles from 1e5 two-stream markers in 1e4 k-means clusters
+    (10 Lloyd iterations + lumping) through swpic_kmeans_lump, device-timed;
+    the FP64/FP32 oracle on a bounded sample (2e4 markers, 1e3 clusters)."""
+    M, K, iters = 100000, 10000, 10
+    m = W.two_stream_markers(M, 7)
+    dev = lambda a, dt=torch.float64: torch.tensor(np.ascontiguousarray(a), device="cuda", dtype=dt)
+    Qm, Pm, wm = dev(m["Q"]), dev(m["P"]), dev(m["psi"])
+    outs = [torch.zeros(K, dtype=torch.float64, device="cuda") for _ in range(5)]
+    assign = torch.zeros(M, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    L = 2 * np.pi
+
+    def call():
+        cq, cp = dev(m["Q"][:K]), dev(m["P"][:K])
+        return swpic.swpic_kmeans_lump(Qm.data_ptr(), Pm.data_ptr(), wm.data_ptr(), M, cq.data_ptr(),
+                                       cp.data_ptr(), K, L, iters, assign.data_ptr(),
+                                       *[o.data_ptr() for o in outs], stream.cuda_stream)
+    call()
+    best = 1e30
+    n = 0
+    for _ in range(3):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        n = call()
+        e1.record(stream)
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    evals = M * K * (iters + 1)
+    return {"markers": M, "clusters": K, "iterations": iters, "decorated_particles": int(n),
+            "gpu_ms": best, "center_distance_evals_per_s": evals / (best / 1e3),
+            "note": "the oracle's rate on a bounded sample is in cpu_baseline.init_kmeans"}
 
 
 def ensemble_leg(torch, swpic):
@@ -480,7 +517,22 @@ def cpu_baseline_leg(spec, args):
     return {"value": n * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d of %d lattice columns (%d particles) of %s, %d steps, single-threaded "
                       "plain-C FP64 oracle (includes its one-time dense LU of the Poisson matrix)" %
-                      (cols, spec.lattice.nq, n, spec.name, k)}
+                      (cols, spec.lattice.nq, n, spec.name, k),
+            "init_kmeans": kmeans_oracle_sample()}
+
+
+def kmeans_oracle_sample():
+    """The oracle's k-means initialization on a bounded sample: 2e4 two-stream
+    markers, 1e3 clusters, 8 Lloyd iterations + lumping, one core."""
+    import oracle as O
+    Ms, Ks, its, L = 20000, 1000, 8, 2 * np.pi
+    m = W.two_stream_markers(Ms, 1)
+    t0 = time.perf_counter()
+    cq, cp, a = O.kmeans(m["Q"], m["P"], m["psi"], m["Q"][:Ks], m["P"][:Ks], L, its)
+    O.lump(m["Q"], m["P"], m["psi"], a, cq, cp, L)
+    t = time.perf_counter() - t0
+    return {"markers": Ms, "clusters": Ks, "iterations": its, "seconds": t, "cores": 1,
+            "center_distance_evals_per_s": Ms * Ks * (its + 1) / t}
 
 
 if __name__ == "__main__":
