@@ -326,8 +326,15 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
         }
         if (lane < nw) sh_ll[lane] = x;                          // inclusive warp totals
         if (lane == nw - 1) {
-            long long qq = x / nx, rr = x % nx;
-            if (rr < 0) { rr += nx; qq -= 1; }
+            long long qq, rr;
+            if ((nx & (nx - 1)) == 0) {                         // nx = 2^m: floor shift, low bits
+                qq = x >> (__ffs(nx) - 1);
+                rr = x & (long long)(nx - 1);
+            } else {
+                qq = x / nx;
+                rr = x % nx;
+                if (rr < 0) { rr += nx; qq -= 1; }
+            }
             sh_ll[32] = qq;
             sh_ll[33] = rr;
         }
@@ -355,22 +362,40 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
     if (lane == 0) { sh_q[0][warp] = es; sh_q[1][warp] = e2; }
     __syncthreads();
     const double inv = R.fx_inv;
-    // 4. thread 0: gauge mean m = esum / nx (an integer part refined exactly
-    //    from a double estimate, and a fraction), field energy about the
-    //    reference, sum (e - m)^2 = sum (e - c)^2 - nx (m - c)^2 (no
-    //    cancellation while c is near m), W = (h/2) sum e^2 2^-2k, E_amp.
-    //    No FP64 division or square root in the FP32 path: they are long
-    //    serial sequences on this GPU's narrow FP64 pipe.
+    // 4. gauge mean m = esum / nx as an integer part and a fraction: for
+    //    nx = 2^m every thread takes it from the shift and the low bits of the
+    //    exact sum; otherwise thread 0 refines a double estimate exactly.
+    long long mean_i, mrem;
+    const bool pow2 = (nx & (nx - 1)) == 0;
+    if (pow2) {
+        __int128 esum = 0;
+        for (int w = 0; w < nw; ++w) esum += sh_q[0][w];
+        mean_i = (long long)(esum >> (__ffs(nx) - 1));
+        mrem = (long long)(esum & (__int128)(nx - 1));
+    } else {
+        if (tid == 0) {
+            __int128 esum = 0;
+            for (int w = 0; w < nw; ++w) esum += sh_q[0][w];
+            long long mi = (long long)floor(i128_to_double(esum) * R.inv_nx);
+            __int128 rr = esum - (__int128)mi * nx;
+            while (rr < 0) { rr += nx; --mi; }
+            while (rr >= nx) { rr -= nx; ++mi; }
+            sh_ll[0] = mi;
+            sh_ll[1] = (long long)rr;
+        }
+        __syncthreads();
+        mean_i = sh_ll[0];
+        mrem = sh_ll[1];
+    }
+    //    Thread 0 then computes the field energy about the reference while
+    //    the other warps build the table: sum (e - m)^2 = sum (e - c)^2 -
+    //    nx (m - c)^2 (no cancellation while c is near m), W = (h/2) sum e^2
+    //    2^-2k, E_amp.  No FP64 division or square root in the FP32 path:
+    //    they are long serial sequences on this GPU's narrow FP64 pipe.
     if (tid == 0) {
-        __int128 esum = 0, e2sum = 0;
-        for (int w = 0; w < nw; ++w) { esum += sh_q[0][w]; e2sum += sh_q[1][w]; }
-        long long mi = (long long)floor(i128_to_double(esum) * R.inv_nx);
-        __int128 rr = esum - (__int128)mi * nx;
-        while (rr < 0) { rr += nx; --mi; }
-        while (rr >= nx) { rr -= nx; ++mi; }
-        sh_ll[0] = mi;
-        sh_ll[1] = (long long)rr;
-        const double d8 = ((double)(mi - c) + (double)rr * R.inv_nx) * (1.0 / 256.0);
+        __int128 e2sum = 0;
+        for (int w = 0; w < nw; ++w) e2sum += sh_q[1][w];
+        const double d8 = ((double)(mean_i - c) + (double)mrem * R.inv_nx) * (1.0 / 256.0);
         const double sc = inv * 256.0;                          // undo the >> 8
         double E2 = (i128_to_double(e2sum) - (double)nx * d8 * d8) * sc * sc;
         if (E2 < 0.0) E2 = 0.0;
@@ -380,11 +405,14 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
         else Ea = sqrt(E2 * R.inv_nx);
         a.field_diag[2 * r] = W;
         a.field_diag[2 * r + 1] = Ea;
-        a.gauge[r] = mi;
+        a.gauge[r] = mean_i;
         if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
     }
-    __syncthreads();
-    const long long mean_i = sh_ll[0];
+    // the table nodes go to the threads after warp 0 (all threads if there is one warp)
+    const int tb = (nt > 32) ? 32 : 0, nt2 = nt - tb;
+    const int per2 = (nx + nt2 - 1) / nt2;
+    const int t2 = tid - tb;
+    const int k0 = (t2 < 0) ? nx : min(nx, t2 * per2), k1 = (t2 < 0) ? nx : min(nx, k0 + per2);
     // 5. the (phi_h', phi_h'') table
     T2 *tab = reinterpret_cast<T2 *>(a.table) + off;
     if (sizeof(T) == 4) {
@@ -392,7 +420,7 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
         // gauge/remainder terms (< nx quanta) are below FP32 resolution
         const float finv = opaque((float)inv);                  // power of two: exact
         const float f_inv_h = opaque((float)R.inv_h), f_half_inv_h = opaque((float)(0.5 * R.inv_h));
-        for (int j = j0; j < j1; ++j) {
+        for (int j = k0; j < k1; ++j) {
             const int jm = (j == 0) ? nx - 1 : j - 1, jp = (j == nx - 1) ? 0 : j + 1;
             const long long ej_i = s_p[j], em_i = s_p[jm], ep_i = s_p[jp];
             const long long btj = (j == 0) ? ej_i : ej_i - em_i;
@@ -403,13 +431,13 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
             tab[j] = t;
         }
     } else {
-        const double mfrac = (double)sh_ll[1] * R.inv_nx;
+        const double mfrac = (double)mrem * R.inv_nx;
         const double rem_node = (double)rem * inv * R.inv_nx;
         const double cen = 0.5 * (double)(nx + 1);
         auto efield = [&](long long eint, int kk) {
             return ((double)(eint - mean_i) - mfrac) * inv - ((double)(kk + 1) - cen) * rem_node;
         };
-        for (int j = j0; j < j1; ++j) {
+        for (int j = k0; j < k1; ++j) {
             const int jm = (j == 0) ? nx - 1 : j - 1, jp = (j == nx - 1) ? 0 : j + 1;
             const long long ej_i = s_p[j], em_i = s_p[jm], ep_i = s_p[jp];
             const long long btj = (j == 0) ? ej_i : ej_i - em_i;
