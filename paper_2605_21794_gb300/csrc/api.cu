@@ -386,6 +386,8 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
         d.h = c.L / c.nx;
         d.inv_h = (double)c.nx / c.L;
         d.inv_nx = 1.0 / (double)c.nx;
+        d.inv_nxf = (float)d.inv_nx;
+        d.hf = (float)(c.L / (double)c.nx);
         d.inv_L = 1.0 / c.L;
         d.dt = c.dt;
         d.Lf = (float)c.L;

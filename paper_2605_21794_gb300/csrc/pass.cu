@@ -265,6 +265,23 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
 __device__ __forceinline__ double i128_to_double(__int128 v) {
     return (double)(long long)(v >> 64) * 18446744073709551616.0 + (double)(unsigned long long)v;
 }
+// nearest float to an unsigned 64-bit integer (ties to even), integer operations only
+__device__ __forceinline__ float ull_to_float(unsigned long long ax) {
+    if (ax == 0ull) return 0.0f;
+    const int lz = __clzll((long long)ax);
+    const unsigned long long m = ax << lz;
+    unsigned mant = (unsigned)(m >> 40);
+    const unsigned long long rest = m & 0xFFFFFFFFFFull, half = 0x8000000000ull;
+    mant += (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
+    return __uint_as_float(((unsigned)(190 - lz) << 23) + (mant - 0x800000u));
+}
+// a non-negative int128 as a float (the low bits beyond 64 are dropped first)
+__device__ __forceinline__ float u128_to_float(__int128 v) {
+    const unsigned long long hi = (unsigned long long)(v >> 64);
+    if (hi == 0ull) return ull_to_float((unsigned long long)v);
+    const int sh = 64 - __clzll((long long)hi);
+    return scalbnf(ull_to_float((unsigned long long)(v >> sh)), sh);
+}
 // nearest float to a 64-bit integer (ties to even, as a conversion rounds),
 // from integer operations only: the conversion instruction runs on the
 // narrow FP64/conversion pipe of this GPU
@@ -395,18 +412,36 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
     if (tid == 0) {
         __int128 e2sum = 0;
         for (int w = 0; w < nw; ++w) e2sum += sh_q[1][w];
-        const double d8 = ((double)(mean_i - c) + (double)mrem * R.inv_nx) * (1.0 / 256.0);
-        const double sc = inv * 256.0;                          // undo the >> 8
-        double E2 = (i128_to_double(e2sum) - (double)nx * d8 * d8) * sc * sc;
-        if (E2 < 0.0) E2 = 0.0;
-        const double W = 0.5 * R.h * E2;
-        double Ea;
-        if (sizeof(T) == 4) Ea = (double)sqrtf((float)(E2 * R.inv_nx));   // FP32 state: FP32 precision
-        else Ea = sqrt(E2 * R.inv_nx);
-        a.field_diag[2 * r] = W;
-        a.field_diag[2 * r + 1] = Ea;
+        bool done = false;
+        if (sizeof(T) == 4) {
+            // FP32 state: FP32 diagnostics from integer-converted sums (no FP64
+            // latency chain), unless the reference is far from the new mean
+            const float e2f = u128_to_float(e2sum);
+            const float d8f = (ll_to_float(mean_i - c) + ll_to_float(mrem) * R.inv_nxf) * (1.0f / 256.0f);
+            const float sub = (float)nx * d8f * d8f;
+            if (sub <= 0.25f * e2f) {
+                const int ke = (int)((__double_as_longlong(inv) >> 52) & 0x7ff) - 1023 + 8;   // inv 2^8 = 2^ke
+                const float E2f = scalbnf(e2f - sub, 2 * ke);
+                a.field_diag[2 * r] = (double)(0.5f * R.hf * E2f);
+                a.field_diag[2 * r + 1] = (double)sqrtf(E2f * R.inv_nxf);
+                if (!isfinite(E2f)) atomicOr(a.err + r, kErrNonFinite);
+                done = true;
+            }
+        }
+        if (!done) {
+            const double d8 = ((double)(mean_i - c) + (double)mrem * R.inv_nx) * (1.0 / 256.0);
+            const double sc = inv * 256.0;                      // undo the >> 8
+            double E2 = (i128_to_double(e2sum) - (double)nx * d8 * d8) * sc * sc;
+            if (E2 < 0.0) E2 = 0.0;
+            const double W = 0.5 * R.h * E2;
+            double Ea;
+            if (sizeof(T) == 4) Ea = (double)sqrtf((float)(E2 * R.inv_nx));   // FP32 state: FP32 precision
+            else Ea = sqrt(E2 * R.inv_nx);
+            a.field_diag[2 * r] = W;
+            a.field_diag[2 * r + 1] = Ea;
+            if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
+        }
         a.gauge[r] = mean_i;
-        if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
     }
     // the table nodes go to the threads after warp 0 (all threads if there is one warp)
     const int tb = (nt > 32) ? 32 : 0, nt2 = nt - tb;

@@ -60,6 +60,7 @@ struct RunDev {
     float Lf, inv_hf, inv_Lf, dtf;  // FP32 copies (rounded once from the FP64 values)
     float inv_hf_lo;         // (nx/L) - inv_hf, so Q nx/L = Q inv_hf + Q inv_hf_lo to ~2^-48
     float L_lo;              // L - Lf: the FP32 domain is [0, Lf + L_lo) in exact terms
+    float hf, inv_nxf;       // FP32 h and 1/nx (diagnostics of FP32 runs)
     int32_t nx, mesh_off;
 };
 
