@@ -71,6 +71,12 @@ def lib():
         L.or_kmeans.restype = None
         L.or_lump.argtypes = [C.c_int64, _D, _D, _D, _I32, C.c_int32, C.c_double, _D, _D, _D, _D, _D, _D, _D]
         L.or_lump.restype = C.c_int64
+        L.or_p2_field.argtypes = [C.c_int64, _D, _D, _D, _I32, C.c_double, C.c_int32, _D, _D, _D]
+        L.or_p2_field.restype = C.c_int
+        L.or_p2_gather.argtypes = [C.c_int64, _D, _I32, C.c_double, C.c_int32, _D, _D, _D, _D]
+        L.or_p2_gather.restype = None
+        L.or_p2_energy.argtypes = [C.c_int32, C.c_double, _D, _D, _D, _D]
+        L.or_p2_energy.restype = None
         L.or_init_lattice.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double,
                                       C.c_double, C.c_double, C.c_double, C.c_int32,
                                       _D, _D, _D, _D, _D, C.c_int32, C.c_int32, _D, _D,
@@ -97,7 +103,7 @@ def _f64(a):
     return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
 
 
-D2_LUMPED, D2_CONSISTENT, D2_NODAL = 0, 1, 2
+D2_LUMPED, D2_CONSISTENT, D2_NODAL, D2_P2 = 0, 1, 2, 3
 
 
 def wrap(Q, L):
@@ -330,3 +336,29 @@ def lump(Qm, Pm, wm, assign, cq, cp, L):
                       *[_d(a) for a in out])
     Q, P, qs, ps, psi = [a[:n].copy() for a in out]
     return {"Q": Q, "P": P, "qs": qs, "ps": ps, "psi": psi}
+
+
+# --- P2 (quadratic Lagrange) elements ---
+def p2_field(Q, p_star, psi_star, L, nx, elem=None):
+    """P2 Galerkin field: (Phi2 [2 nx], a [nx], beta [nx]) with
+    phi_h'(xi) = a + beta (1 - 2 xi) and phi_h'' = -2 beta / h on each element."""
+    Q, ps, psi = _f64(Q), _f64(p_star), _f64(psi_star)
+    e = None if elem is None else np.ascontiguousarray(elem, dtype=np.int32)
+    Phi2, a, beta = np.zeros(2 * nx), np.zeros(nx), np.zeros(nx)
+    rc = lib().or_p2_field(len(Q), _d(Q), _d(ps), _d(psi), _i(e), L, nx, _d(Phi2), _d(a), _d(beta))
+    if rc != 0:
+        raise RuntimeError("P2 solve failed")
+    return Phi2, a, beta
+
+
+def p2_gather(Q, a, beta, L, nx):
+    Q = _f64(Q)
+    dV, d2V = np.zeros(len(Q)), np.zeros(len(Q))
+    lib().or_p2_gather(len(Q), _d(Q), None, L, nx, _d(_f64(a)), _d(_f64(beta)), _d(dV), _d(d2V))
+    return dV, d2V
+
+
+def p2_energy(a, beta, L):
+    W, E = C.c_double(), C.c_double()
+    lib().or_p2_energy(len(a), L, _d(_f64(a)), _d(_f64(beta)), C.byref(W), C.byref(E))
+    return W.value, E.value

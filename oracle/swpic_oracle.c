@@ -417,6 +417,13 @@ typedef struct {
     int32_t *elem;     /* FP32-storage element decisions (store_f32 only) */
 } or_field;
 
+/* P2 elements (d2_mode 3): defined below */
+int or_p2_field(int64_t n, const double *Q, const double *p_star, const double *psi_star,
+                const int32_t *elem, double L, int32_t nx, double *Phi2, double *a_el, double *beta_el);
+void or_p2_gather(int64_t n, const double *Q, const int32_t *elem, double L, int32_t nx,
+                  const double *a_el, const double *beta_el, double *dV, double *d2V);
+void or_p2_energy(int32_t nx, double L, const double *a_el, const double *beta_el, double *W, double *E_amp);
+
 static void decide_elements(or_field *f, int64_t n, const double *Q) {
     for (int64_t a = 0; a < n; ++a) f->elem[a] = or_element_f32(Q[a], f->L, f->nx);
 }
@@ -424,6 +431,17 @@ static void decide_elements(or_field *f, int64_t n, const double *Q) {
 static int field_update(or_field *f, int64_t n, const double *Q, const double *p_star,
                         const double *psi_star) {
     if (f->store_f32) decide_elements(f, n, Q);
+    if (f->d2_mode == 3) {
+        /* P2: dphi <- a (element midpoint phi'), d2 <- beta; Phi <- vertex values */
+        double *Phi2 = (double *)malloc(sizeof(double) * 2 * (size_t)f->nx);
+        int rc = or_p2_field(n, Q, f->decorated ? p_star : NULL, psi_star, f->store_f32 ? f->elem : NULL,
+                             f->L, f->nx, Phi2, f->dphi, f->d2);
+        for (int32_t j = 0; j < f->nx; ++j) f->Phi[j] = Phi2[2 * j];
+        free(Phi2);
+        if (f->store_f32)
+            for (int32_t j = 0; j < f->nx; ++j) { f->dphi[j] = to_f32(f->dphi[j]); f->d2[j] = to_f32(f->d2[j]); }
+        return rc;
+    }
     or_deposit(n, Q, f->decorated ? p_star : NULL, psi_star, f->store_f32 ? f->elem : NULL,
                f->L, f->nx, f->b);
     double lambda = 0.0;
@@ -457,6 +475,10 @@ static void write_diag(double *rec, double t, int64_t n, const double *P, const 
                        const double *psi_star, const or_field *f) {
     double out[6];
     or_diagnostics(n, P, f->decorated ? q_star : NULL, psi_star, f->nx, f->L, f->Phi, out);
+    if (f->d2_mode == 3) {        /* P2: field energy and E_amp of the quadratic phi_h */
+        or_p2_energy(f->nx, f->L, f->dphi, f->d2, &out[3], &out[5]);
+        out[4] = out[2] + out[3];
+    }
     rec[0] = t;
     for (int k = 0; k < 6; ++k) rec[1 + k] = out[k];
 }
@@ -487,14 +509,16 @@ int or_run(int64_t n, double *Q, double *P, double *q_star, double *p_star,
     const double half = store_f32 ? to_f32(0.5 * dt) : 0.5 * dt;
     const double full = store_f32 ? to_f32(dt) : dt;
     for (int32_t s = 1; rc == 0 && s <= n_steps; ++s) {
-        or_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
+        if (d2_mode == 3) or_p2_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, f.dV, f.d2V);
+        else or_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
         or_kick_values(n, ps, P, qs, f.dV, f.d2V, half);
         store_state(&f, n, NULL, P, qs, NULL);
         or_drift(n, Q, P, qs, ps, L, full);
         store_state(&f, n, Q, P, qs, ps);
         rc = field_update(&f, n, Q, ps, psi_star);
         if (rc != 0) break;
-        or_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
+        if (d2_mode == 3) or_p2_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, f.dV, f.d2V);
+        else or_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
         or_kick_values(n, ps, P, qs, f.dV, f.d2V, half);
         store_state(&f, n, NULL, P, qs, NULL);
         if (diag && diag_every > 0 && s % diag_every == 0)
@@ -769,4 +793,92 @@ int64_t or_lump(int64_t M, const double *Qm, const double *Pm, const double *wm,
     }
     free(mq); free(mp); free(ws); free(a0); free(best); free(slot);
     return n;
+}
+
+/* ------------------------------------------------------------------------ */
+/* P2 (quadratic Lagrange) elements, V_h^(2) of Sec. 5 (degree k = 2):       */
+/* phi_h' and phi_h'' both come from the element's quadratic, no projection. */
+/* Degrees of freedom: vertex j -> 2j, midpoint of element i -> 2i + 1      */
+/* (2 nx in all, periodic).  On element i with xi = (Q - q_i)/h:             */
+/*   N_v0 = (1-xi)(1-2xi), N_m = 4 xi (1-xi), N_v1 = xi (2xi - 1),           */
+/*   h N' = (4xi - 3, 4 - 8xi, 4xi - 1).                                     */
+/* Eq. lin-sys with the P2 stiffness (element (1/3h)[[7,-8,1],[-8,16,-8],    */
+/* [1,-8,7]]), Eq. rhs-assembly b_k = sum psi N_k(Q) - p* N_k'(Q), and the   */
+/* zero-mean test space as a bordered system with c_k = int N_k (h/3 per    */
+/* vertex, 2h/3 per midpoint): A Phi + lambda c = b, c^T Phi = 0.  Dense.    */
+/* Outputs per element i: a_i = phi_h' at the element midpoint and           */
+/* beta_i with phi_h'(xi) = a_i + beta_i (1 - 2 xi), phi_h'' = -2 beta_i/h.  */
+/* ------------------------------------------------------------------------ */
+static void p2_basis(double xi, double h, double N[3], double dN[3]) {
+    N[0] = (1.0 - xi) * (1.0 - 2.0 * xi);
+    N[1] = 4.0 * xi * (1.0 - xi);
+    N[2] = xi * (2.0 * xi - 1.0);
+    dN[0] = (4.0 * xi - 3.0) / h;
+    dN[1] = (4.0 - 8.0 * xi) / h;
+    dN[2] = (4.0 * xi - 1.0) / h;
+}
+
+int or_p2_field(int64_t n, const double *Q, const double *p_star, const double *psi_star,
+                const int32_t *elem, double L, int32_t nx, double *Phi2, double *a_el, double *beta_el) {
+    const int32_t nd = 2 * nx, m = nd + 1;
+    const double h = L / (double)nx;
+    double *M = (double *)calloc((size_t)m * m, sizeof(double));
+    int32_t *piv = (int32_t *)calloc((size_t)m, sizeof(int32_t));
+    double *x = (double *)calloc((size_t)m, sizeof(double));
+    if (!M || !piv || !x) { free(M); free(piv); free(x); return -1; }
+    static const double K[3][3] = {{7, -8, 1}, {-8, 16, -8}, {1, -8, 7}};
+    for (int32_t e = 0; e < nx; ++e) {
+        const int32_t d[3] = {2 * e, 2 * e + 1, (2 * e + 2) % nd};
+        for (int r = 0; r < 3; ++r)
+            for (int c = 0; c < 3; ++c) M[(size_t)d[r] * m + d[c]] += K[r][c] / (3.0 * h);
+        M[(size_t)d[0] * m + nd] += h / 6.0;
+        M[(size_t)d[2] * m + nd] += h / 6.0;
+        M[(size_t)d[1] * m + nd] += 2.0 * h / 3.0;
+        M[(size_t)nd * m + d[0]] += h / 6.0;
+        M[(size_t)nd * m + d[2]] += h / 6.0;
+        M[(size_t)nd * m + d[1]] += 2.0 * h / 3.0;
+    }
+    for (int64_t a = 0; a < n; ++a) {
+        const int32_t e = elem ? elem[a] : or_element(Q[a], L, nx);
+        const double xi = (Q[a] - (double)e * h) / h;
+        double N[3], dN[3];
+        p2_basis(xi, h, N, dN);
+        const int32_t d[3] = {2 * e, 2 * e + 1, (2 * e + 2) % nd};
+        for (int k = 0; k < 3; ++k)
+            x[d[k]] += psi_star[a] * N[k] - (p_star ? p_star[a] : 0.0) * dN[k];
+    }
+    x[nd] = 0.0;
+    int rc = lu_factor(m, M, piv);
+    if (rc == 0) {
+        lu_solve(m, M, piv, x);
+        for (int32_t k = 0; k < nd; ++k) Phi2[k] = x[k];
+        for (int32_t e = 0; e < nx; ++e) {
+            const double v0 = x[2 * e], vm = x[2 * e + 1], v1 = x[(2 * e + 2) % nd];
+            a_el[e] = (v1 - v0) / h;                           /* phi' at xi = 1/2 */
+            beta_el[e] = (4.0 * vm - 2.0 * v0 - 2.0 * v1) / h;  /* phi'(xi) = a + beta (1 - 2 xi) */
+        }
+    }
+    free(M); free(piv); free(x);
+    return rc;
+}
+
+/* phi_h'(Q) and phi_h''(Q) from the P2 element tables */
+void or_p2_gather(int64_t n, const double *Q, const int32_t *elem, double L, int32_t nx,
+                  const double *a_el, const double *beta_el, double *dV, double *d2V) {
+    const double h = L / (double)nx;
+    for (int64_t a = 0; a < n; ++a) {
+        const int32_t e = elem ? elem[a] : or_element(Q[a], L, nx);
+        const double xi = (Q[a] - (double)e * h) / h;
+        dV[a] = a_el[e] + beta_el[e] * (1.0 - 2.0 * xi);
+        d2V[a] = -2.0 * beta_el[e] / h;
+    }
+}
+
+/* W = (1/2) int phi_h'^2 = (h/2) sum (a^2 + beta^2/3); E_amp = ((1/L) int phi_h'^2)^(1/2) */
+void or_p2_energy(int32_t nx, double L, const double *a_el, const double *beta_el, double *W, double *E_amp) {
+    const double h = L / (double)nx;
+    double s = 0.0;
+    for (int32_t e = 0; e < nx; ++e) s += h * (a_el[e] * a_el[e] + beta_el[e] * beta_el[e] / 3.0);
+    *W = 0.5 * s;
+    *E_amp = sqrt(s / L);
 }
