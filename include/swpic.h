@@ -73,8 +73,13 @@ typedef enum swpic_deposit_mode {
  * LUMPED: g = lumped-mass L2 projection of phi_h' onto P1, g_j =
  *         (Phi_{j+1} - Phi_{j-1})/(2h); phi'' = g' (constant per element).
  * NODAL:  s_j = -btilde_j/h, the lumped L2 projection of phi'' = n0 - rho
- *         (Eq. poisson), interpolated linearly inside each element.     */
-typedef enum swpic_d2_mode { SWPIC_D2_LUMPED = 0, SWPIC_D2_NODAL = 2 } swpic_d2_mode;
+ *         (Eq. poisson), interpolated linearly inside each element.
+ * P2:     the field itself in V_h^(2) (quadratic Lagrange elements, the
+ *         degree-k space of Sec. 5 with k = 2): phi_h' is linear and phi_h''
+ *         constant inside each element, both from the element's quadratic,
+ *         no projection.  The deposit adds one accumulator per element
+ *         (the midpoint degree of freedom).                              */
+typedef enum swpic_d2_mode { SWPIC_D2_LUMPED = 0, SWPIC_D2_NODAL = 2, SWPIC_D2_P2 = 3 } swpic_d2_mode;
 
 typedef struct swpic_config {
     double  L;                 /* domain length (> 0)                            */

@@ -56,6 +56,7 @@ struct swpic_ctx {
     std::vector<RunDev> h_runs;
     unsigned long long *d_acc = nullptr, *d_done = nullptr;
     long long *d_snap = nullptr, *d_gauge = nullptr;
+    unsigned long long *d_acc_m = nullptr;     // P2 element-midpoint load
     void *d_table = nullptr;
     double *d_b = nullptr, *d_bt = nullptr, *d_e = nullptr, *d_phi = nullptr;
     double *d_diag_acc = nullptr, *d_field_diag = nullptr, *d_mass = nullptr, *d_mabs = nullptr;
@@ -144,7 +145,10 @@ swpic_status validate_cfg(const swpic_config &c, std::string &why) {
     if (c.precision != SWPIC_F32 && c.precision != SWPIC_F64) { why = "precision must be 32 or 64"; return SWPIC_EINVAL; }
     if (c.decorated != 0 && c.decorated != 1) { why = "decorated must be 0 or 1"; return SWPIC_EINVAL; }
     if (c.deposit_mode != 0 && c.deposit_mode != 1) { why = "bad deposit_mode"; return SWPIC_EINVAL; }
-    if (c.d2_mode != SWPIC_D2_LUMPED && c.d2_mode != SWPIC_D2_NODAL) { why = "bad d2_mode"; return SWPIC_EINVAL; }
+    if (c.d2_mode != SWPIC_D2_LUMPED && c.d2_mode != SWPIC_D2_NODAL && c.d2_mode != SWPIC_D2_P2) {
+        why = "bad d2_mode";
+        return SWPIC_EINVAL;
+    }
     if (c.resort_every < 0) { why = "resort_every must be >= 0"; return SWPIC_EINVAL; }
     if (c.threads_per_block != 0 &&
         (c.threads_per_block < 64 || c.threads_per_block > 512 || c.threads_per_block % 32)) {
@@ -160,7 +164,7 @@ void free_all(swpic_ctx *ctx) {
     ctx->graph_cache.clear();
     for (auto ev : ctx->events) cudaEventDestroy(ev);
     ctx->events.clear();
-    void *ptrs[] = {ctx->d_runs, ctx->d_acc, ctx->d_snap, ctx->d_gauge, ctx->d_done, ctx->d_table, ctx->d_b, ctx->d_bt, ctx->d_e,
+    void *ptrs[] = {ctx->d_runs, ctx->d_acc, ctx->d_acc_m, ctx->d_snap, ctx->d_gauge, ctx->d_done, ctx->d_table, ctx->d_b, ctx->d_bt, ctx->d_e,
                     ctx->d_phi, ctx->d_diag_acc, ctx->d_field_diag, ctx->d_mass, ctx->d_mabs,
                     ctx->d_steps, ctx->d_ring, ctx->d_ring_count, ctx->d_err, ctx->d_chunks,
                     ctx->d_cnt, ctx->d_pos, ctx->d_scan_tmp, ctx->d_partials};
@@ -186,6 +190,7 @@ PassArgs base_args(swpic_ctx *ctx) {
     a.acc = ctx->d_acc;
     a.snap = ctx->d_snap;
     a.gauge = ctx->d_gauge;
+    a.acc_m = ctx->d_acc_m;
     a.table = ctx->d_table;
     a.b = ctx->d_b; a.btilde = ctx->d_bt; a.efield = ctx->d_e;
     a.run_done = ctx->d_done;
@@ -210,7 +215,7 @@ int pass_stages(const swpic_ctx *ctx) {
     budget = std::min(budget, ctx->smem_block > kPassStaticSmem ? ctx->smem_block - kPassStaticSmem : 0);
     int S = 0;
     for (int k = std::min(ctx->pipe, 8); k >= 2; --k)
-        if (pass_smem_bytes(ctx->prec, ctx->max_nx, ctx->mode, ctx->dec, ctx->tpb, k) <= budget) { S = k; break; }
+        if (pass_smem_bytes(ctx->prec, ctx->max_nx, ctx->mode, ctx->dec, ctx->tpb, k, ctx->d2) <= budget) { S = k; break; }
     return S;
 }
 
@@ -244,7 +249,7 @@ swpic_status enqueue_pass(swpic_ctx *ctx, double c1, double c2, double cd, uint3
     pass_shape(ctx, &grid, &chunk);
     a.chunk = chunk;
     a.stages = pass_stages(ctx);
-    const size_t smem = pass_smem_bytes(ctx->prec, ctx->max_nx, ctx->mode, ctx->dec, ctx->tpb, a.stages);
+    const size_t smem = pass_smem_bytes(ctx->prec, ctx->max_nx, ctx->mode, ctx->dec, ctx->tpb, a.stages, ctx->d2);
     if (ctx->N > 0) {
         CK(launch_pass(ctx->prec, ctx->dec, ctx->mode, a, grid, ctx->tpb, smem, ctx->stream));
         ctx->launches += 1;
@@ -302,6 +307,7 @@ swpic_status prepare(swpic_ctx *ctx, bool keep_steps) {
     s = upload_runs(ctx);
     if (s != SWPIC_OK) return s;
     CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_acc_m, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_done, 0, sizeof(unsigned long long) * ctx->R, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_diag_acc, 0, sizeof(double) * 2 * ctx->R, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t) * ctx->R, ctx->stream));
@@ -434,6 +440,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
     ok &= alloc((void **)&ctx->d_acc, sizeof(unsigned long long) * mo);
     ok &= alloc((void **)&ctx->d_snap, sizeof(long long) * mo);
     ok &= alloc((void **)&ctx->d_gauge, sizeof(long long) * R);
+    ok &= alloc((void **)&ctx->d_acc_m, sizeof(unsigned long long) * mo);
     ok &= alloc((void **)&ctx->d_done, sizeof(unsigned long long) * R);
     ok &= alloc(&ctx->d_table, (size_t)mo * 2 * es);
     ok &= alloc((void **)&ctx->d_b, sizeof(double) * mo);
@@ -465,6 +472,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
     cudaMemset(ctx->d_acc, 0, sizeof(unsigned long long) * mo);
     cudaMemset(ctx->d_snap, 0, sizeof(long long) * mo);
     cudaMemset(ctx->d_gauge, 0, sizeof(long long) * R);
+    cudaMemset(ctx->d_acc_m, 0, sizeof(unsigned long long) * mo);
     cudaMemset(ctx->d_done, 0, sizeof(unsigned long long) * R);
     cudaMemset(ctx->d_steps, 0, sizeof(long long) * R);
     cudaMemset(ctx->d_ring_count, 0, sizeof(int32_t) * R);
@@ -691,6 +699,7 @@ swpic_status swpic_deposit(swpic_ctx *ctx) {
     swpic_status s = ensure_prepared(ctx);
     if (s != SWPIC_OK) return s;
     CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_acc_m, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
     s = enqueue_pass(ctx, 0.0, 0.0, 0.0, PASS_DEPOSIT | PASS_NO_WRITE, false);
     if (s != SWPIC_OK) return s;
     PassArgs b = base_args(ctx);

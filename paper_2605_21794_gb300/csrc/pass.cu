@@ -298,7 +298,7 @@ __device__ __forceinline__ float ll_to_float(long long x) {
 }
 
 // One CTA.  full = false: snapshot only (swpic_deposit's read-out).
-template <typename T>
+template <typename T, bool P2>
 __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned char *smem, bool full) {
     using T2 = typename Vec2<T>::type;
     __shared__ long long sh_ll[34];
@@ -448,8 +448,12 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
     const int per2 = (nx + nt2 - 1) / nt2;
     const int t2 = tid - tb;
     const int k0 = (t2 < 0) ? nx : min(nx, t2 * per2), k1 = (t2 < 0) ? nx : min(nx, k0 + per2);
-    // 5. the (phi_h', phi_h'') table
+    // 5. the (phi_h', phi_h'') table.  P2: phi_h'(xi) = -e + beta (1 - 2 xi) with
+    //    beta = (3/4) btilde_m, btilde_m = b_m - (2/3) S/nx (the midpoint load
+    //    less its share of the uniform background), from exact integers
     T2 *tab = reinterpret_cast<T2 *>(a.table) + off;
+    constexpr bool p2 = P2;
+    double beta2 = 0.0;
     if (sizeof(T) == 4) {
         // FP32 table straight from the exact integers; the sub-quantum
         // gauge/remainder terms (< nx quanta) are below FP32 resolution
@@ -461,8 +465,17 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
             const long long btj = (j == 0) ? ej_i : ej_i - em_i;
             T2 t;
             t.x = (T)(-(ll_to_float(ej_i - mean_i) * finv));
-            if (a.d2_mode == SWPIC_D2_NODAL) t.y = (T)(-ll_to_float(btj) * finv * f_inv_h);
-            else t.y = (T)(ll_to_float(em_i - ep_i) * finv * f_half_inv_h);
+            if constexpr (p2) {
+                const long long bm = (long long)__ldcg(a.acc_m + off + j);
+                a.acc_m[off + j] = 0ull;
+                const float beta = (0.25f * ll_to_float(3 * bm - 2 * q) - 0.5f * ll_to_float(rem) * R.inv_nxf) * finv;
+                t.y = (T)beta;
+                beta2 += (double)(beta * beta);
+            } else if (a.d2_mode == SWPIC_D2_NODAL) {
+                t.y = (T)(-ll_to_float(btj) * finv * f_inv_h);
+            } else {
+                t.y = (T)(ll_to_float(em_i - ep_i) * finv * f_half_inv_h);
+            }
             tab[j] = t;
         }
     } else {
@@ -478,9 +491,29 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
             const long long btj = (j == 0) ? ej_i : ej_i - em_i;
             T2 t;
             t.x = (T)(-efield(ej_i, j));
-            if (a.d2_mode == SWPIC_D2_NODAL) t.y = (T)(-((double)btj * inv - rem_node) * R.inv_h);
-            else t.y = (T)((efield(em_i, jm) - efield(ep_i, jp)) * (0.5 * R.inv_h));
+            if constexpr (p2) {
+                const long long bm = (long long)__ldcg(a.acc_m + off + j);
+                a.acc_m[off + j] = 0ull;
+                const double beta = (0.25 * (double)(3 * bm - 2 * q) - 0.5 * (double)rem * R.inv_nx) * inv;
+                t.y = (T)beta;
+                beta2 += beta * beta;
+            } else if (a.d2_mode == SWPIC_D2_NODAL) {
+                t.y = (T)(-((double)btj * inv - rem_node) * R.inv_h);
+            } else {
+                t.y = (T)((efield(em_i, jm) - efield(ep_i, jp)) * (0.5 * R.inv_h));
+            }
             tab[j] = t;
+        }
+    }
+    if constexpr (p2) {
+        // P2 field energy: (1/2) int phi'^2 = (h/2) sum (e^2 + beta^2/3); E_amp = (2W/L)^(1/2)
+        __shared__ double sh_b[32];
+        const double b2 = block_sum_d(beta2, sh_b);
+        if (tid == 0) {
+            const double W = a.field_diag[2 * r] + R.h * b2 / 6.0;
+            a.field_diag[2 * r] = W;
+            a.field_diag[2 * r + 1] = sqrt(2.0 * W * R.inv_nx / R.h);
+            if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
         }
     }
 }
@@ -585,12 +618,18 @@ template <typename T, bool DEC, bool DEP, bool DIAG, int D2>
 __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
                                          const typename Vec2<T>::type *tab, const int nx,
                                          const Geo<T> &G, const T k1, const T k2, const T kd,
-                                         T &dm, T &dk, int &key, T &w0, T &w1) {
+                                         T &dm, T &dk, int &key, T &w0, T &w1, T &wm) {
     T p0, f0;
     const int i = elem_of(Q, G, p0, f0);
     const auto f = tab[i];
     T d2 = T(0);
-    if (DEC) {
+    T d1 = f.x;                                 // phi_h'(Q)
+    if (D2 == SWPIC_D2_P2) {
+        // P2: phi_h' = a + beta (1 - 2 xi), phi_h'' = -2 beta / h on the element
+        const T xi = xi_of(Q, p0, f0, G);
+        d1 = fma(f.y, T(1) - T(2) * xi, f.x);
+        if (DEC) d2 = T(-2) * G.inv_h * f.y;
+    } else if (DEC) {
         if (D2 == SWPIC_D2_NODAL) {
             const T xi = xi_of(Q, p0, f0, G);
             const T g1 = tab[i + 1 == nx ? 0 : i + 1].y;
@@ -600,14 +639,14 @@ __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
         }
     }
     // closing half-kick of the previous step
-    P = fma(-k1, f.x, P);
+    P = fma(-k1, d1, P);
     if (DEC) qs = fma(k1 * ps, d2, qs);
     if (DIAG) {
         dm = DEC ? fma(w, P, qs) : w * P;                                 // momentum density
         dk = DEC ? fma(T(0.5) * w * P, P, qs * P) : T(0.5) * w * P * P;  // kinetic density
     }
     // opening half-kick of the next step
-    P = fma(-k2, f.x, P);
+    P = fma(-k2, d1, P);
     if (DEC) qs = fma(k2 * ps, d2, qs);
     // drift
     Q = drift_wrap(Q, P, kd, G);
@@ -623,6 +662,13 @@ __device__ __forceinline__ void push_one(T &Q, T &P, T &qs, T &ps, const T w,
         } else {
             w0 = w * (T(1) - xi);
             w1 = w * xi;
+        }
+        // P2: the vertex loads condense exactly to w0, w1 above; the midpoint
+        // load psi* N_m(xi) - p* N_m'(xi), N_m = 4 xi (1 - xi), goes to its own
+        // accumulator
+        if (D2 == SWPIC_D2_P2) {
+            wm = T(4) * w * xi * (T(1) - xi);
+            if (DEC) wm = fma(-ps * G.inv_h, T(4) - T(8) * xi, wm);
         }
     }
 }
@@ -650,10 +696,10 @@ template <typename T>
 struct VecOut {
     static constexpr int n = Vec16<T>::n;
     int key[n];
-    T w0[n], w1[n];
+    T w0[n], w1[n], wm[n];       // wm: P2 midpoint load (unused otherwise)
     __device__ __forceinline__ void clear() {
 #pragma unroll
-        for (int l = 0; l < n; ++l) { key[l] = -1; w0[l] = T(0); w1[l] = T(0); }
+        for (int l = 0; l < n; ++l) { key[l] = -1; w0[l] = T(0); w1[l] = T(0); wm[l] = T(0); }
     }
 };
 
@@ -675,11 +721,18 @@ __device__ __forceinline__ void push_vector(typename Vec16<T>::type &q, typename
         T qs = DEC ? X[l] : T(0), ps = DEC ? Y[l] : T(0);
         T dm = T(0), dk = T(0);
         push_one<T, DEC, DEP, DIAG, D2>(Q[l], P[l], qs, ps, M[l], s_tab, nx, G, k1, k2, kd, dm, dk,
-                                        o.key[l], o.w0[l], o.w1[l]);
+                                        o.key[l], o.w0[l], o.w1[l], o.wm[l]);
         if (DIAG) { vm += dm; vk += dk; }
         if (DEC) { X[l] = qs; Y[l] = ps; }
     }
     if (DIAG) { th.mom.add(vm); th.kin.add(vk); }
+}
+
+// P2: one particle's midpoint load into the CTA's per-element mesh
+template <typename T, int MODE>
+__device__ __forceinline__ void mesh_m_add(int key, T v, void *mesh_m, T scale, int32_t *err) {
+    if (MODE == SWPIC_DEPOSIT_ATOMIC) atomicAdd(reinterpret_cast<T *>(mesh_m) + key, v);
+    else atomicAdd(reinterpret_cast<unsigned long long *>(mesh_m) + key, to_fixed(v, scale, err));
 }
 
 // Deposit one vector per lane.  Runs of equal elements inside the vector are
@@ -687,9 +740,15 @@ __device__ __forceinline__ void push_vector(typename Vec16<T>::type &q, typename
 // one warp-aggregated deposit (so a sorted or cold plasma, where whole
 // vectors share an element, costs one shared atomic per segment of lanes),
 // later runs go to the mesh directly.  All lanes of the warp must call this.
-template <typename T, int MODE>
-__device__ __forceinline__ void deposit_vector(const VecOut<T> &o, void *s_mesh, T scale, int32_t *err) {
+template <typename T, int MODE, bool P2>
+__device__ __forceinline__ void deposit_vector(const VecOut<T> &o, void *s_mesh, void *s_mesh_m, T scale,
+                                               int32_t *err) {
     constexpr int VW = Vec16<T>::n;
+    if (P2) {
+#pragma unroll
+        for (int l = 0; l < VW; ++l)
+            if (o.key[l] >= 0) mesh_m_add<T, MODE>(o.key[l], o.wm[l], s_mesh_m, scale, err);
+    }
     const int k0 = o.key[0];
     T s0 = o.w0[0], s1 = o.w1[0];
     bool first = true;
@@ -727,7 +786,7 @@ template <typename T> struct TurnVecs {
 
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
 __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, int64_t e,
-                                const typename Vec2<T>::type *s_tab, void *s_mesh, Thread<T> &th,
+                                const typename Vec2<T>::type *s_tab, void *s_mesh, void *s_mesh_m, Thread<T> &th,
                                 int32_t *err) {
     using V = typename Vec16<T>::type;
     constexpr int VW = Vec16<T>::n;
@@ -750,14 +809,15 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
         T Q = Qi[k], P = Pi[k], w = wi[k];
         T qs = DEC ? qsi[k] : T(0), ps = DEC ? psi[k] : T(0);
         int key = -1;
-        T w0 = T(0), w1 = T(0), dm = T(0), dk = T(0);
-        push_one<T, DEC, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, dm, dk, key, w0, w1);
+        T w0 = T(0), w1 = T(0), wm = T(0), dm = T(0), dk = T(0);
+        push_one<T, DEC, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, dm, dk, key, w0, w1, wm);
         if (DIAG) { th.mom.add(dm); th.kin.add(dk); }
         Qo[k] = Q;
         Po[k] = P;
         if (DEC) { qso[k] = qs; pso[k] = ps; }
         if (wpsi) wo[k] = w;
         if (DEP) mesh_add<T, MODE>(key, w0, w1, s_mesh, scale, err);
+        if (DEP && D2 == SWPIC_D2_P2) mesh_m_add<T, MODE>(key, wm, s_mesh_m, scale, err);
     };
 
     constexpr int A = AlignOf<T>::n;
@@ -808,7 +868,7 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
             } else {
                 o.clear();
             }
-            if (DEP) deposit_vector<T, MODE>(o, s_mesh, scale, err);
+            if (DEP) deposit_vector<T, MODE, D2 == SWPIC_D2_P2>(o, s_mesh, s_mesh_m, scale, err);
         }
     }
     for (int64_t k = ve + threadIdx.x; k < e; k += blockDim.x) scalar(k);
@@ -881,6 +941,13 @@ template <typename T, int MODE>
 __host__ __device__ __forceinline__ size_t mesh_bytes(int max_nx) {
     return (size_t)(max_nx + 1) * (MODE == SWPIC_DEPOSIT_ATOMIC ? sizeof(T) : sizeof(unsigned long long));
 }
+// node mesh plus, for P2, the per-element midpoint mesh
+template <typename T, int MODE, int D2>
+__host__ __device__ __forceinline__ size_t mesh_bytes_all(int max_nx) {
+    return mesh_bytes<T, MODE>(max_nx) +
+           (D2 == SWPIC_D2_P2 ? (size_t)max_nx * (MODE == SWPIC_DEPOSIT_ATOMIC ? sizeof(T) : sizeof(unsigned long long))
+                              : 0);
+}
 
 // Shared-memory layout of the pass: table | mesh | (bulk stream) mbarriers | stages.
 __host__ __device__ __forceinline__ size_t round128(size_t x) { return (x + 127) / 128 * 128; }
@@ -902,7 +969,7 @@ struct Pipe {
 
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
 __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t s, int64_t e,
-                                     const typename Vec2<T>::type *s_tab, void *s_mesh, Thread<T> &th,
+                                     const typename Vec2<T>::type *s_tab, void *s_mesh, void *s_mesh_m, Thread<T> &th,
                                      int32_t *err, Pipe &pp, int *s_abort) {
     using V = typename Vec16<T>::type;
     constexpr int VW = Vec16<T>::n;
@@ -927,14 +994,15 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
         T Q = Qi[k], P = Pi[k], w = wi[k];
         T qs = DEC ? qsi[k] : T(0), ps = DEC ? psi[k] : T(0);
         int key = -1;
-        T w0 = T(0), w1 = T(0), dm = T(0), dk = T(0);
-        push_one<T, DEC, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, dm, dk, key, w0, w1);
+        T w0 = T(0), w1 = T(0), wm = T(0), dm = T(0), dk = T(0);
+        push_one<T, DEC, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, dm, dk, key, w0, w1, wm);
         if (DIAG) { th.mom.add(dm); th.kin.add(dk); }
         Qo[k] = Q;
         Po[k] = P;
         if (DEC) { qso[k] = qs; pso[k] = ps; }
         if (wpsi) wo[k] = w;
         if (DEP) mesh_add<T, MODE>(key, w0, w1, s_mesh, scale, err);
+        if (DEP && D2 == SWPIC_D2_P2) mesh_m_add<T, MODE>(key, wm, s_mesh_m, scale, err);
     };
 
     constexpr int A = AlignOf<T>::n;
@@ -1016,7 +1084,7 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
             } else {
                 o.clear();
             }
-            if (DEP) deposit_vector<T, MODE>(o, s_mesh, scale, err);
+            if (DEP) deposit_vector<T, MODE, D2 == SWPIC_D2_P2>(o, s_mesh, s_mesh_m, scale, err);
         }
     }
     if (!ok && lane == 0) {
@@ -1033,13 +1101,13 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
     return *s_abort == 0;
 }
 
-template <typename T>
+template <typename T, bool P2>
 __device__ void finish_run(const PassArgs &a, const RunDev &R, int r, unsigned char *smem) {
     const uint32_t fl = a.flags;
     const bool diag = (fl & PASS_DIAG) != 0;
     DiagPre pre;
     if (diag && threadIdx.x == 0) diag_preload(a, r, pre);
-    if (fl & PASS_SOLVE) solve_run<T>(a, R, r, smem, true);
+    if (fl & PASS_SOLVE) solve_run<T, P2>(a, R, r, smem, true);
     if (threadIdx.x == 0) {
         if (diag) diag_write(a, R, r, pre);
         if (fl & PASS_COUNT_STEP) a.steps[r] += 1;
@@ -1055,10 +1123,12 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
     __shared__ double s_red[64];
     T2 *s_tab = reinterpret_cast<T2 *>(smem);
     void *s_mesh = smem + (size_t)a.max_nx * sizeof(T2);
+    // P2: the per-element midpoint mesh follows the node mesh (same element type)
+    void *s_mesh_m = reinterpret_cast<unsigned char *>(s_mesh) + mesh_bytes<T, MODE>(a.max_nx);
     const bool bulk = a.stages >= 2;
     Pipe pp;
     {
-        const size_t tb = (size_t)a.max_nx * sizeof(T2), mb = mesh_bytes<T, MODE>(a.max_nx);
+        const size_t tb = (size_t)a.max_nx * sizeof(T2), mb = mesh_bytes_all<T, MODE, D2>(a.max_nx);
         const int nw = blockDim.x >> 5, w = threadIdx.x >> 5;
         constexpr size_t stage_bytes = (DEC ? 5 : 3) * TurnVecs<T>::n * sizeof(typename Vec16<T>::type);
         pp.S = a.stages;
@@ -1094,9 +1164,14 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
             if (MODE == SWPIC_DEPOSIT_ATOMIC) {
                 T *m = reinterpret_cast<T *>(s_mesh);
                 for (int j = threadIdx.x; j <= nx; j += blockDim.x) m[j] = T(0);
+                if (D2 == SWPIC_D2_P2)
+                    for (int j = threadIdx.x; j < nx; j += blockDim.x) reinterpret_cast<T *>(s_mesh_m)[j] = T(0);
             } else {
                 unsigned long long *m = reinterpret_cast<unsigned long long *>(s_mesh);
                 for (int j = threadIdx.x; j <= nx; j += blockDim.x) m[j] = 0ull;
+                if (D2 == SWPIC_D2_P2)
+                    for (int j = threadIdx.x; j < nx; j += blockDim.x)
+                        reinterpret_cast<unsigned long long *>(s_mesh_m)[j] = 0ull;
             }
         }
         __syncthreads();
@@ -1104,11 +1179,11 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
         th.mom = {T(0), T(0)};
         th.kin = {T(0), T(0)};
         if (bulk) {
-            if (!process_segment_bulk<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, th, a.err + r,
+            if (!process_segment_bulk<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, s_mesh_m, th, a.err + r,
                                                                   pp, &s_abort))
                 return;      // a copy did not arrive: the run's flag says so
         } else {
-            process_segment<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, th, a.err + r);
+            process_segment<T, DEC, MODE, DEP, DIAG, D2>(a, R, s, e, s_tab, s_mesh, s_mesh_m, th, a.err + r);
         }
         // every CTA has been scheduled by now: let the next pass launch early
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
@@ -1123,6 +1198,18 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
                 } else {
                     const unsigned long long v = reinterpret_cast<unsigned long long *>(s_mesh)[j];
                     if (v != 0ull) atomicAdd(gacc + node, v);
+                }
+            }
+            if (D2 == SWPIC_D2_P2) {
+                unsigned long long *gm = a.acc_m + R.mesh_off;
+                for (int j = threadIdx.x; j < nx; j += blockDim.x) {
+                    if (MODE == SWPIC_DEPOSIT_ATOMIC) {
+                        const T v = reinterpret_cast<T *>(s_mesh_m)[j];
+                        if (v != T(0)) atomicAdd(gm + j, to_fixed(v, (T)R.fx_scale, a.err + r));
+                    } else {
+                        const unsigned long long v = reinterpret_cast<unsigned long long *>(s_mesh_m)[j];
+                        if (v != 0ull) atomicAdd(gm + j, v);
+                    }
                 }
             }
         }
@@ -1150,7 +1237,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
             __syncthreads();
             if (s_last) {
                 __threadfence();
-                finish_run<T>(a, R, r, smem);
+                finish_run<T, D2 == SWPIC_D2_P2>(a, R, r, smem);
             }
         }
         __syncthreads();
@@ -1188,7 +1275,8 @@ __global__ void __launch_bounds__(1024) k_solve_runs(PassArgs a, int full) {
     if (r >= a.n_runs) return;
     const RunDev R = a.runs[r];
     if (full == 2) readout_run(a, R, smem);
-    else solve_run<T>(a, R, r, smem, full != 0);
+    else if (a.d2_mode == SWPIC_D2_P2) solve_run<T, true>(a, R, r, smem, full != 0);
+    else solve_run<T, false>(a, R, r, smem, full != 0);
 }
 
 // Phi from e: Phi_{j+1} = Phi_j - h e_j, then zero mean (one CTA per run)
@@ -1227,10 +1315,11 @@ __global__ void __launch_bounds__(1024) k_phi(const RunDev *runs, int n_runs, co
 // ---------------------------------------------------------------------------
 size_t solve_smem_bytes(int max_nx) { return (size_t)max_nx * 8; }
 
-size_t pass_smem_bytes(int prec, int max_nx, int mode, bool decorated, int tpb, int stages) {
+size_t pass_smem_bytes(int prec, int max_nx, int mode, bool decorated, int tpb, int stages, int d2_mode) {
     const size_t t2 = (prec == SWPIC_F64) ? 16 : 8;
     const size_t me = (mode == SWPIC_DEPOSIT_ATOMIC) ? ((prec == SWPIC_F64) ? 8 : 4) : 8;
-    const size_t tb = (size_t)max_nx * t2, mb = (size_t)(max_nx + 1) * me;
+    const size_t tb = (size_t)max_nx * t2,
+                 mb = (size_t)(max_nx + 1) * me + (d2_mode == SWPIC_D2_P2 ? (size_t)max_nx * me : 0);
     size_t push = tb + mb;
     if (stages >= 2)
         push = stage_area_offset(tb, mb, tpb / 32, stages) +
@@ -1261,7 +1350,12 @@ static cudaError_t launch_pass_t(const PassArgs &a, int grid, int tpb, size_t sm
         cfg.numAttrs = 1;                                                                         \
         return cudaLaunchKernelEx(&cfg, kern, a);                                                 \
     } while (0)
-    if (nodal) {
+    if (a.d2_mode == SWPIC_D2_P2) {
+        if (dep && diag) SWPIC_LAUNCH(true, true, SWPIC_D2_P2);
+        if (dep) SWPIC_LAUNCH(true, false, SWPIC_D2_P2);
+        if (diag) SWPIC_LAUNCH(false, true, SWPIC_D2_P2);
+        SWPIC_LAUNCH(false, false, SWPIC_D2_P2);
+    } else if (nodal) {
         if (dep && diag) SWPIC_LAUNCH(true, true, SWPIC_D2_NODAL);
         if (dep) SWPIC_LAUNCH(true, false, SWPIC_D2_NODAL);
         if (diag) SWPIC_LAUNCH(false, true, SWPIC_D2_NODAL);

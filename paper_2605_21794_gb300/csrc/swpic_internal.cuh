@@ -88,6 +88,7 @@ struct PassArgs {
     unsigned long long *acc;  // int64 bit patterns
     long long *snap;          // int64 snapshot of acc taken by the last solve (read-out)
     long long *gauge;         // [R] integer gauge mean of the last solve (reference of the next)
+    unsigned long long *acc_m;  // P2: int64 bit patterns of the element-midpoint load (per element)
     void *table;              // T2 per element
     double *b, *btilde, *efield;
     unsigned long long *run_done;
@@ -102,7 +103,7 @@ struct PassArgs {
 };
 
 // shared-memory bytes of the pass kernel / the per-run solve for a given max nx
-size_t pass_smem_bytes(int prec, int max_nx, int mode, bool decorated, int tpb, int stages);
+size_t pass_smem_bytes(int prec, int max_nx, int mode, bool decorated, int tpb, int stages, int d2_mode);
 size_t solve_smem_bytes(int max_nx);
 
 // launchers (return cudaError_t of the launch)

@@ -21,7 +21,7 @@ SWPIC_OK, SWPIC_EINVAL, SWPIC_ENOMEM, SWPIC_ECUDA = 0, 1, 2, 3
 SWPIC_ETIMEOUT, SWPIC_ENUMERIC, SWPIC_EUNSUPPORTED, SWPIC_ESTATE, SWPIC_EIO = 4, 5, 6, 7, 8
 SWPIC_F32, SWPIC_F64 = 32, 64
 SWPIC_DEPOSIT_ATOMIC, SWPIC_DEPOSIT_DETERMINISTIC = 0, 1
-SWPIC_D2_LUMPED, SWPIC_D2_NODAL = 0, 2
+SWPIC_D2_LUMPED, SWPIC_D2_NODAL, SWPIC_D2_P2 = 0, 2, 3
 SWPIC_NX_MAX = 4096
 
 
