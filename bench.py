@@ -38,6 +38,7 @@ UNIT = "decorated particle-steps/s"
 # algorithmic bytes per particle-step of the fused pass: read Q,P,q*,p*,psi*, write Q,P,q*,p*
 BYTES_PER_PARTICLE = {(32, True): 36, (64, True): 72, (32, False): 20, (64, False): 40}
 FALLBACK_HBM_GBS = 6800.0
+D2_MODES = {"lumped": 0, "nodal": 2, "p2": 3}      # swpic_d2_mode values
 
 
 def parse():
@@ -55,6 +56,8 @@ def parse():
     ap.add_argument("--side", type=int, default=4096, help="lattice side (4096 = the workload)")
     ap.add_argument("--launch", default=None, help="TPBxBPSM: fixed launch shape (no autotune)")
     ap.add_argument("--stages", type=int, default=None, help="bulk-copy stages (0 = register loads; no autotune)")
+    ap.add_argument("--d2-mode", choices=list(D2_MODES), default="lumped",
+                    help="phi'' of the kick: P1 field with a lumped or nodal projection, or the P2 field")
     return ap.parse_args()
 
 
@@ -169,14 +172,14 @@ def oracle_sample_spec(spec, cols):
     return dataclasses.replace(spec.lattice, nq=cols)
 
 
-def time_oracle(spec, cols, steps, warmup, diag_every):
+def time_oracle(spec, cols, steps, warmup, diag_every, d2_mode=0):
     import oracle as O
     lat = oracle_sample_spec(spec, cols)
     st = O.init_lattice(lat)
     if warmup > 0:
-        st = O.run(st, spec.nx, lat.L, spec.dt, warmup, diag_every=diag_every)
+        st = O.run(st, spec.nx, lat.L, spec.dt, warmup, diag_every=diag_every, d2_mode=d2_mode)
     t0 = time.perf_counter()
-    O.run(st, spec.nx, lat.L, spec.dt, steps, diag_every=diag_every)
+    O.run(st, spec.nx, lat.L, spec.dt, steps, diag_every=diag_every, d2_mode=d2_mode)
     dt = time.perf_counter() - t0
     return lat.n, dt
 
@@ -186,17 +189,21 @@ def run_reference(args, spec):
     if rank != 0:
         return
     cols = max(1, min(spec.lattice.nq, 16))           # 16 x 4096 = 65,536 particles per step
-    n, dt = time_oracle(spec, cols, args.steps, args.warmup, args.diag_every)
-    value = n * args.steps / dt
+    d2 = D2_MODES[args.d2_mode]
+    # the oracle's P2 field is a dense (2 nx + 1)^2 solve every step: a few steps only
+    steps = min(args.steps, 5) if d2 == 3 else args.steps
+    warm = min(args.warmup, 1) if d2 == 3 else args.warmup
+    n, dt = time_oracle(spec, cols, steps, warm, args.diag_every, d2)
+    value = n * steps / dt
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": workload_config(spec, args, None),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d of %d lattice columns (%d particles) of %s, %d steps, "
                                        "single-threaded plain-C FP64 oracle" %
-                                       (cols, spec.lattice.nq, n, spec.name, args.steps)},
+                                       (cols, spec.lattice.nq, n, spec.name, steps)},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -204,7 +211,7 @@ def run_reference(args, spec):
 def workload_config(spec, args, resort):
     return {"workload": spec.name, "particles": spec.lattice.n, "lattice": [spec.lattice.nq, spec.lattice.nv],
             "nx": spec.nx, "dt": spec.dt, "L": spec.lattice.L, "precision": "fp32 state, fp64 solve",
-            "deposit_mode": args.deposit_mode, "diag_every": args.diag_every,
+            "deposit_mode": args.deposit_mode, "d2_mode": args.d2_mode, "diag_every": args.diag_every,
             "resort_every": resort,
             "l2": "inputs larger than L2 (FP32 state %.0f MB > 129 MB)" % (spec.lattice.n * 20 / 1e6),
             "parallelism": "replicas (one independent run per GPU)"}
@@ -231,7 +238,8 @@ def main():
 
     def make(mode_, resort, graphs=True):
         s = swpic.Simulation([(lat.L, spec.dt, spec.nx, n)], precision=32, deposit_mode=mode_,
-                             resort_every=max(resort, 0), use_graphs=graphs, diag_capacity=64)
+                             d2_mode=D2_MODES[args.d2_mode], resort_every=max(resort, 0),
+                             use_graphs=graphs, diag_capacity=64)
         s.init_lattice(0, lat)
         swpic.swpic_refresh(s.ctx)
         return s
@@ -312,7 +320,8 @@ def main():
     traffic = profiled_traffic()
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_pass<float, decorated, %s, deposit, diag>" % args.deposit_mode,
+                "kernel": "k_pass<float, decorated, %s, deposit, diag%s>" % (
+                    args.deposit_mode, ", P2" if args.d2_mode == "p2" else ""),
                 "algorithmic_bytes_per_launch": bpp * n,
                 "avg_launch_ms": avg_pass_ms, "peak_source": peak_src,
                 "step_frac": (bpp * n * world / (ms / args.steps / 1e3) / 1e9) / peak}
@@ -341,6 +350,8 @@ def main():
         line["e2e"] = e2e_leg(torch, swpic, sim, n, args)
         line["batched_vs_plain"] = ensemble_leg(torch, swpic)
         line["init_kmeans"] = kmeans_leg(torch, swpic)
+        if args.d2_mode != "p2":
+            line["p2_elements"] = p2_leg(torch, swpic, spec, args, (tpb, bpsm, resort, stages), timed)
         line["cpu_baseline"] = cpu_baseline_leg(spec, args)
     elif rank == 0:
         restore(sim)
@@ -425,6 +436,62 @@ def kmeans_leg(torch, swpic):
     return {"markers": M, "clusters": K, "iterations": iters, "decorated_particles": int(n),
             "gpu_ms": best, "center_distance_evals_per_s": evals / (best / 1e3),
             "note": "the oracle's rate on a bounded sample is in cpu_baseline.init_kmeans"}
+
+
+def p2_leg(torch, swpic, spec, args, launch, timed):
+    """The same workload with the field in quadratic Lagrange elements (Sec. 5,
+    k = 2), device-timed like the main line; then the energy behaviour of the
+    P1 field with each phi'' projection and of the P2 field over warm-up + K
+    steps from t = 0 (Hamiltonian sampled every 10 steps)."""
+    lat = spec.lattice
+    n = lat.n
+    tpb, bpsm, resort, stages = launch
+
+    def make(d2, cap):
+        s = swpic.Simulation([(lat.L, spec.dt, spec.nx, n)], precision=32, d2_mode=d2,
+                             resort_every=max(resort, 0), diag_capacity=cap)
+        swpic.swpic_set_launch(s.ctx, tpb, bpsm, resort)
+        swpic.swpic_set_pipeline(s.ctx, stages)
+        s.init_lattice(0, lat)
+        swpic.swpic_refresh(s.ctx)
+        return s
+
+    s = make(swpic.SWPIC_D2_P2, 64)
+    s.step(args.warmup, args.diag_every)
+    ms = timed(s, args.steps)
+    s.close()
+    # per-pass device durations over the same warm-up + K steps from t = 0
+    s = make(swpic.SWPIC_D2_P2, 64)
+    s.step(args.warmup, args.diag_every)
+    swpic.swpic_set_timing(s.ctx, 1)
+    s.step(args.steps, args.diag_every)
+    pass_ms = swpic.swpic_pass_times(s.ctx)
+    s.close()
+    avg_pass_ms = float(np.mean(pass_ms[1:-1] if len(pass_ms) > 2 else pass_ms))
+    bpp = BYTES_PER_PARTICLE[(32, True)]
+    peak, peak_src = measured_peak()
+    achieved = bpp * n / (avg_pass_ms / 1e3) / 1e9
+    every, total = 10, args.warmup + args.steps
+    energy = {}
+    for d2, name in ((swpic.SWPIC_D2_LUMPED, "p1_lumped"), (swpic.SWPIC_D2_NODAL, "p1_nodal"),
+                     (swpic.SWPIC_D2_P2, "p2")):
+        s = make(d2, total // every + 8)
+        s.step(total, every)
+        d = s.diagnostics()
+        s.close()
+        H, Wf = d[:, 5], d[:, 4]
+        energy[name] = {"max_abs_dH": float(np.max(np.abs(H - H[0]))),
+                        "max_abs_dH_over_H0": float(np.max(np.abs(H - H[0])) / abs(H[0])),
+                        "max_abs_dH_over_max_W": float(np.max(np.abs(H - H[0])) / np.max(Wf)),
+                        "W_final_over_W0": float(Wf[-1] / Wf[0])}
+    return {"value": n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "d2_mode": "P2",
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_pass_ms,
+                         "kernel": "k_pass<float, decorated, atomic, deposit, diag, P2>",
+                         "algorithmic_bytes_per_launch": bpp * n, "peak_source": peak_src},
+            "energy_behaviour": energy, "energy_steps": total, "energy_sample_every": every,
+            "note": "the oracle's P2 rate on a bounded sample is in cpu_baseline.p2_elements"}
 
 
 def ensemble_leg(torch, swpic):
@@ -518,7 +585,17 @@ def cpu_baseline_leg(spec, args):
             "sample": "%d of %d lattice columns (%d particles) of %s, %d steps, single-threaded "
                       "plain-C FP64 oracle (includes its one-time dense LU of the Poisson matrix)" %
                       (cols, spec.lattice.nq, n, spec.name, k),
-            "init_kmeans": kmeans_oracle_sample()}
+            "init_kmeans": kmeans_oracle_sample(), "p2_elements": p2_oracle_sample(spec, args)}
+
+
+def p2_oracle_sample(spec, args):
+    """The oracle with the P2 field (a dense (2 nx + 1)^2 LU solve every step)
+    on 64 lattice columns, 3 steps, one core."""
+    cols, k = 64, 3
+    n, dt = time_oracle(spec, cols, k, 0, args.diag_every, 3)
+    return {"value": n * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d of %d lattice columns (%d particles), %d steps, P2 field" %
+                      (cols, spec.lattice.nq, n, k)}
 
 
 def kmeans_oracle_sample():
