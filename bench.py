@@ -317,7 +317,8 @@ def main():
     bpp = BYTES_PER_PARTICLE[(32, True)]
     achieved = bpp * n / (avg_pass_ms / 1e3) / 1e9
     peak, peak_src = measured_peak()
-    traffic = profiled_traffic()
+    traffic = profiled_traffic("k_pass_p2_bump_on_tail_4096" if args.d2_mode == "p2" else
+                               "k_pass_bump_on_tail_4096")
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
                 "kernel": "k_pass<float, decorated, %s, deposit, diag%s>" % (
@@ -363,12 +364,12 @@ def main():
         torch.distributed.destroy_process_group()
 
 
-def profiled_traffic():
+def profiled_traffic(name="k_pass_bump_on_tail_4096"):
     """DRAM bytes per launch of the fused pass from the committed ncu summary,
     valid only while the kernel source is the one that was profiled."""
     import hashlib
     src = os.path.join(ROOT, "paper_2605_21794_gb300", "csrc", "pass.cu")
-    summ = os.path.join(ROOT, "profiles", "k_pass_bump_on_tail_4096.json")
+    summ = os.path.join(ROOT, "profiles", name + ".json")
     try:
         with open(summ) as f:
             d = json.load(f)
@@ -446,6 +447,7 @@ def p2_leg(torch, swpic, spec, args, launch, timed):
     lat = spec.lattice
     n = lat.n
     tpb, bpsm, resort, stages = launch
+    tuned = False
 
     def make(d2, cap):
         s = swpic.Simulation([(lat.L, spec.dt, spec.nx, n)], precision=32, d2_mode=d2,
@@ -456,6 +458,16 @@ def p2_leg(torch, swpic, spec, args, launch, timed):
         swpic.swpic_refresh(s.ctx)
         return s
 
+    if args.resort < 0 and not args.no_autotune and args.launch is None and args.stages is None:
+        # P2 adds one shared atomic per particle: tune its own launch shape and
+        # resort cadence on the state after the lattice order is gone
+        s = make(swpic.SWPIC_D2_P2, 64)
+        s.step(max(args.warmup, 300), args.diag_every)
+        swpic.swpic_autotune(s.ctx, 30, None)
+        tpb, bpsm, resort = swpic.swpic_get_launch(s.ctx)
+        stages = swpic.swpic_get_pipeline(s.ctx)[1]
+        s.close()
+        tuned = True
     s = make(swpic.SWPIC_D2_P2, 64)
     s.step(args.warmup, args.diag_every)
     ms = timed(s, args.steps)
@@ -486,8 +498,11 @@ def p2_leg(torch, swpic, spec, args, launch, timed):
                         "W_final_over_W0": float(Wf[-1] / Wf[0])}
     return {"value": n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "d2_mode": "P2",
+            "launch": {"threads_per_block": tpb, "blocks_per_sm": bpsm, "bulk_copy_stages": stages,
+                       "resort_every": resort, "autotuned": tuned},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg_pass_ms,
+                         "frac": achieved / peak, "traffic": profiled_traffic("k_pass_p2_bump_on_tail_4096"),
+                         "avg_launch_ms": avg_pass_ms,
                          "kernel": "k_pass<float, decorated, atomic, deposit, diag, P2>",
                          "algorithmic_bytes_per_launch": bpp * n, "peak_source": peak_src},
             "energy_behaviour": energy, "energy_steps": total, "energy_sample_every": every,
