@@ -81,6 +81,29 @@ def lib():
                                       C.c_double, C.c_double, C.c_double, C.c_int32,
                                       _D, _D, _D, _D, _D, C.c_int32, C.c_int32, _D, _D,
                                       _D, _D, _D, _D, _D]
+        # 2D2V (swpic2d_oracle.c)
+        L.or2d_cell.restype = C.c_int32
+        L.or2d_cell.argtypes = [C.c_double, C.c_double, C.c_int32]
+        L.or2d_cell_f32.restype = C.c_int32
+        L.or2d_cell_f32.argtypes = [C.c_double, C.c_double, C.c_int32]
+        L.or2d_deposit.restype = None
+        L.or2d_deposit.argtypes = [C.c_int64, _D, _D, _D, _D, _D, _I32, _I32, C.c_double, C.c_double,
+                                   C.c_int32, C.c_int32, _D]
+        L.or2d_stiffness.restype = None
+        L.or2d_stiffness.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, _D]
+        L.or2d_solve.restype = C.c_int
+        L.or2d_solve.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, _D, _D, _D]
+        L.or2d_project.restype = None
+        L.or2d_project.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, _D, _D, _D]
+        L.or2d_gather.restype = None
+        L.or2d_gather.argtypes = [C.c_int64, _D, _D, _I32, _I32, C.c_double, C.c_double, C.c_int32,
+                                  C.c_int32, _D, _D, _D, _D, _D, _D, _D, _D, _D]
+        L.or2d_field_energy.restype = C.c_double
+        L.or2d_field_energy.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, _D]
+        L.or2d_run.restype = C.c_int
+        L.or2d_run.argtypes = [C.c_int64, _D, _D, _D, _D, _D, _D, _D, _D, _D, C.c_int32, C.c_int32,
+                               C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_int32,
+                               _D, _I32, _D, C.c_int32]
         _lib = L
     return _lib
 
@@ -362,3 +385,95 @@ def p2_energy(a, beta, L):
     W, E = C.c_double(), C.c_double()
     lib().or_p2_energy(len(a), L, _d(_f64(a)), _d(_f64(beta)), C.byref(W), C.byref(E))
     return W.value, E.value
+
+
+# ---------------------------------------------------------------------------
+# 2D2V: periodic bilinear (Q1) mesh of nx x ny cells on [0, Lx) x [0, Ly);
+# mesh arrays are (ny, nx), node (i, j) at (i hx, j hy).
+# ---------------------------------------------------------------------------
+STATE2D = ("Qx", "Qy", "Px", "Py", "qx", "qy", "px", "py", "psi")
+
+
+def cell2d(Q, L, n, f32=False):
+    """Cell index along one axis, decided in FP64 (or in FP32 from FP32 values)."""
+    f = lib().or2d_cell_f32 if f32 else lib().or2d_cell
+    return np.array([f(float(q), float(L), int(n)) for q in np.atleast_1d(Q)], dtype=np.int32)
+
+
+def deposit2d(Qx, Qy, psx, psy, psi, Lx, Ly, nx, ny, cx=None, cy=None):
+    """b_j = sum_a psi*_a N_j(Q_a) - p*_a . grad N_j(Q_a)  (Eq. swpic_poisson, S_h = delta)."""
+    Qx, Qy, psi = _f64(Qx), _f64(Qy), _f64(psi)
+    psx, psy = _f64(psx), _f64(psy)
+    cx = None if cx is None else np.ascontiguousarray(cx, dtype=np.int32)
+    cy = None if cy is None else np.ascontiguousarray(cy, dtype=np.int32)
+    b = np.zeros((ny, nx))
+    lib().or2d_deposit(len(Qx), _d(Qx), _d(Qy), _d(psx), _d(psy), _d(psi), _i(cx), _i(cy),
+                       float(Lx), float(Ly), int(nx), int(ny), _d(b))
+    return b
+
+
+def stiffness2d(nx, ny, Lx, Ly):
+    K = np.zeros((nx * ny, nx * ny))
+    lib().or2d_stiffness(int(nx), int(ny), float(Lx), float(Ly), _d(K))
+    return K
+
+
+def solve2d(b, Lx, Ly):
+    """Zero-mean Q1 Galerkin solve of K Phi + lambda m = b; returns (Phi, lambda)."""
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    ny, nx = b.shape
+    Phi = np.zeros_like(b)
+    lam = C.c_double(0.0)
+    if lib().or2d_solve(int(nx), int(ny), float(Lx), float(Ly), _d(b), _d(Phi), C.byref(lam)) != 0:
+        raise RuntimeError("singular 2D system")
+    return Phi, lam.value
+
+
+def project2d(Phi, Lx, Ly):
+    """Lumped-mass projection g of grad phi_h onto Q1 (each component)."""
+    Phi = np.ascontiguousarray(Phi, dtype=np.float64)
+    ny, nx = Phi.shape
+    gx, gy = np.zeros_like(Phi), np.zeros_like(Phi)
+    lib().or2d_project(int(nx), int(ny), float(Lx), float(Ly), _d(Phi), _d(gx), _d(gy))
+    return gx, gy
+
+
+def gather2d(Qx, Qy, Phi, gx, gy, Lx, Ly, cx=None, cy=None):
+    """grad phi_h and H_ik = d_k g_i at the particles: dict Ex, Ey, Hxx, Hxy, Hyx, Hyy."""
+    Qx, Qy = _f64(Qx), _f64(Qy)
+    Phi, gx, gy = (np.ascontiguousarray(a, dtype=np.float64) for a in (Phi, gx, gy))
+    ny, nx = Phi.shape
+    n = len(Qx)
+    out = {k: np.zeros(n) for k in ("Ex", "Ey", "Hxx", "Hxy", "Hyx", "Hyy")}
+    cx = None if cx is None else np.ascontiguousarray(cx, dtype=np.int32)
+    cy = None if cy is None else np.ascontiguousarray(cy, dtype=np.int32)
+    lib().or2d_gather(n, _d(Qx), _d(Qy), _i(cx), _i(cy), float(Lx), float(Ly), int(nx), int(ny),
+                      _d(Phi), _d(gx), _d(gy), *[_d(out[k]) for k in ("Ex", "Ey", "Hxx", "Hxy", "Hyx", "Hyy")])
+    return out
+
+
+def field_energy2d(Phi, Lx, Ly):
+    Phi = np.ascontiguousarray(Phi, dtype=np.float64)
+    ny, nx = Phi.shape
+    return lib().or2d_field_energy(int(nx), int(ny), float(Lx), float(Ly), _d(Phi))
+
+
+def run2d(state, nx, ny, Lx, Ly, dt, n_steps, diag_every=1, decorated=True, store_f32=False):
+    """KDK run of the 2D2V model.  ``state``: dict with the keys of STATE2D
+    (qx, qy, px, py may be None).  Returns the final state, the diagnostics
+    history as (n, 8) [t, mass, mom_x, mom_y, kinetic, W, H, E_amp] and Phi."""
+    st = {k: (np.zeros(len(state["Qx"])) if state.get(k) is None else np.array(state[k], dtype=np.float64))
+          for k in STATE2D}
+    n = len(st["Qx"])
+    n_rec = (n_steps // diag_every + 1) if diag_every > 0 else 0
+    diag = np.zeros((max(n_rec, 1), 8))
+    nd = C.c_int32(0)
+    Phi = np.zeros((ny, nx))
+    rc = lib().or2d_run(n, *[_d(st[k]) for k in STATE2D], int(nx), int(ny), float(Lx), float(Ly),
+                        float(dt), int(bool(decorated)), int(n_steps), int(diag_every), _d(diag),
+                        C.byref(nd), _d(Phi), int(bool(store_f32)))
+    if rc != 0:
+        raise RuntimeError("2D oracle run failed")
+    st["diag"] = diag[: nd.value]
+    st["Phi"] = Phi
+    return st

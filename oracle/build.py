@@ -8,7 +8,7 @@ import subprocess
 import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-SRC = os.path.join(HERE, "swpic_oracle.c")
+SRCS = [os.path.join(HERE, "swpic_oracle.c"), os.path.join(HERE, "swpic2d_oracle.c")]
 OUT_DIR = os.path.join(HERE, "_build")
 OUT = os.path.join(OUT_DIR, "liboracle.so")
 
@@ -16,11 +16,11 @@ OUT = os.path.join(OUT_DIR, "liboracle.so")
 def build(force: bool = False) -> str:
     os.makedirs(OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(OUT)
-            and os.path.getmtime(OUT) >= os.path.getmtime(SRC)):
+            and all(os.path.getmtime(OUT) >= os.path.getmtime(s) for s in SRCS)):
         return OUT
     tmp = OUT + ".tmp%d" % os.getpid()
     cmd = ["gcc", "-O2", "-std=c99", "-Wall", "-fPIC", "-shared",
-           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, SRC, "-lm"]
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, *SRCS, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, OUT)
     return OUT

@@ -200,6 +200,31 @@ def random_state(n: int, L: float, seed: int = 0, vth: float = 1.0, decorated: b
     return {"Q": Q, "P": P, "qs": qs, "ps": ps, "psi": psi}
 
 
+def random_state_2d(n: int, Lx: float, Ly: float, seed: int = 0, vth: float = 1.0,
+                    decorated: bool = True, dipole_scale: float = 0.25, nx: int = 16, ny: int = 16,
+                    alpha: float = 0.0) -> dict:
+    """A seeded random 2D2V state (keys Qx, Qy, Px, Py, qx, qy, px, py, psi):
+    Q ~ U([0, Lx) x [0, Ly)), each P component ~ vth * (sum of 3 uniforms -
+    1.5) * 2, psi* = (Lx Ly / n)(0.5 + U) (1 + alpha cos(2 pi x/Lx) cos(2 pi y/Ly)),
+    p*_x ~ dipole_scale psi* hx U(-1, 1) (and y with hy), q* ~ dipole_scale
+    psi* vth 0.1 U(-1, 1).  FP64 arrays."""
+    u = uniform01(seed, 30, 13 * n).reshape(13, n) if n > 0 else np.zeros((13, 0))
+    Qx, Qy = Lx * u[0], Ly * u[1]
+    Px = vth * 2.0 * (u[2] + u[3] + u[4] - 1.5)
+    Py = vth * 2.0 * (u[5] + u[6] + u[7] - 1.5)
+    psi = (Lx * Ly / max(n, 1)) * (0.5 + u[8]) * (1.0 + alpha * np.cos(2 * np.pi * Qx / Lx) *
+                                                   np.cos(2 * np.pi * Qy / Ly))
+    z = np.zeros(n)
+    if decorated:
+        px = dipole_scale * psi * (Lx / nx) * (2.0 * u[9] - 1.0)
+        py = dipole_scale * psi * (Ly / ny) * (2.0 * u[10] - 1.0)
+        qx = dipole_scale * psi * vth * 0.1 * (2.0 * u[11] - 1.0)
+        qy = dipole_scale * psi * vth * 0.1 * (2.0 * u[12] - 1.0)
+    else:
+        px = py = qx = qy = z
+    return {"Qx": Qx, "Qy": Qy, "Px": Px, "Py": Py, "qx": qx, "qy": qy, "px": px, "py": py, "psi": psi}
+
+
 def two_stream_markers(M: int, seed: int = 0, alpha: float = 0.01, L: float = 2 * np.pi,
                        v0: float = 1.0, vth: float = 0.3) -> dict:
     """A seeded random sample of M marker particles of the two-stream f0 of the
