@@ -353,6 +353,7 @@ def main():
         line["init_kmeans"] = kmeans_leg(torch, swpic)
         if args.d2_mode != "p2":
             line["p2_elements"] = p2_leg(torch, swpic, spec, args, (tpb, bpsm, resort, stages), timed)
+        line["two_d"] = two_d_leg(torch, swpic, args)
         line["cpu_baseline"] = cpu_baseline_leg(spec, args)
     elif rank == 0:
         restore(sim)
@@ -509,6 +510,56 @@ def p2_leg(torch, swpic, spec, args, launch, timed):
             "note": "the oracle's P2 rate on a bounded sample is in cpu_baseline.p2_elements"}
 
 
+BYTES_PER_PARTICLE_2D = {32: 68, 64: 136}     # read Q, P, q*, p* (2 each) and psi*; write all but psi*
+
+
+def two_d_leg(torch, swpic, args):
+    """The 2D2V step (general-d model of Sec. 3.3 on the torus, bilinear
+    elements): 16,777,216 FP32 decorated particles of a seeded 2D Landau-like
+    state on a 32 x 32 mesh of [0, 4 pi)^2, dt 0.1, diagnostics every step;
+    warm-up W steps, K device-timed steps, then the per-pass roofline."""
+    n, L, nx, dt = 1 << 24, 4 * np.pi, 32, 0.1
+    st = W.random_state_2d(n, L, L, seed=2024, nx=nx, ny=nx, alpha=0.1)
+    sim = swpic.Simulation2D(L, L, nx, nx, dt, n, precision=32, diag_capacity=args.warmup + 2 * args.steps + 8)
+    try:
+        sim.init_particles(st)
+        del st
+        sim.step(args.warmup, args.diag_every)
+        swpic.swpic2d_synchronize(sim.ctx)
+        l0 = swpic.swpic2d_launch_count(sim.ctx)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(args.steps, args.diag_every)
+        e1.record(sim.stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        launches = swpic.swpic2d_launch_count(sim.ctx) - l0
+        swpic.swpic2d_set_timing(sim.ctx, 1)
+        sim.step(min(args.steps, 200), args.diag_every)
+        pass_ms = swpic.swpic2d_pass_times(sim.ctx)
+        swpic.swpic2d_set_timing(sim.ctx, 0)
+        d = sim.diagnostics()
+    finally:
+        sim.close()
+    full = pass_ms[1:-1] if len(pass_ms) > 2 else pass_ms
+    avg = float(np.mean(full))
+    bpp = BYTES_PER_PARTICLE_2D[32]
+    peak, peak_src = measured_peak()
+    achieved = bpp * n / (avg / 1e3) / 1e9
+    H = d[:, 6]
+    return {"workload": "landau2d_random_16M_32x32", "particles": n, "mesh": [nx, nx], "dt": dt,
+            "value": n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
+            "gpu_launches": int(launches),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg,
+                         "kernel": "k_pass2d<float, decorated, deposit, diag>",
+                         "algorithmic_bytes_per_launch": bpp * n, "peak_source": peak_src},
+            "max_abs_dH_over_H0": float(np.max(np.abs(H - H[0])) / abs(H[0])),
+            "note": "the oracle's 2D rate on a bounded sample is in cpu_baseline.two_d"}
+
+
 def ensemble_leg(torch, swpic):
     """256 independent Landau runs (uneven lattices 64^2..512^2, nx = side/2,
     800 steps, diagnostics every step): one graph-captured batched context vs
@@ -600,7 +651,22 @@ def cpu_baseline_leg(spec, args):
             "sample": "%d of %d lattice columns (%d particles) of %s, %d steps, single-threaded "
                       "plain-C FP64 oracle (includes its one-time dense LU of the Poisson matrix)" %
                       (cols, spec.lattice.nq, n, spec.name, k),
-            "init_kmeans": kmeans_oracle_sample(), "p2_elements": p2_oracle_sample(spec, args)}
+            "init_kmeans": kmeans_oracle_sample(), "p2_elements": p2_oracle_sample(spec, args),
+            "two_d": two_d_oracle_sample(args)}
+
+
+def two_d_oracle_sample(args):
+    """The 2D oracle on 65,536 particles of the 2D workload's state (same
+    mesh, dt), 5 steps, one core (its dense LU of the 1025 x 1025 bordered
+    system is included)."""
+    import oracle as O
+    n, L, nx, k = 1 << 16, 4 * np.pi, 32, 5
+    st = W.random_state_2d(n, L, L, seed=2024, nx=nx, ny=nx, alpha=0.1)
+    t0 = time.perf_counter()
+    O.run2d(st, nx, nx, L, L, 0.1, k, diag_every=args.diag_every)
+    t = time.perf_counter() - t0
+    return {"value": n * k / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "%d particles of the 2D workload's distribution, 32 x 32 mesh, %d steps" % (n, k)}
 
 
 def p2_oracle_sample(spec, args):

@@ -395,9 +395,16 @@ STATE2D = ("Qx", "Qy", "Px", "Py", "qx", "qy", "px", "py", "psi")
 
 
 def cell2d(Q, L, n, f32=False):
-    """Cell index along one axis, decided in FP64 (or in FP32 from FP32 values)."""
-    f = lib().or2d_cell_f32 if f32 else lib().or2d_cell
-    return np.array([f(float(q), float(L), int(n)) for q in np.atleast_1d(Q)], dtype=np.int32)
+    """Cell index along one axis: floor(Q / h) clamped to [0, n-1], decided in
+    FP64, or with f32 as or2d_cell_f32 does, floor(fl32(fl32(Q) fl32(n/L)))
+    (elementwise numpy arithmetic; the C routines take the same decisions)."""
+    Q = np.atleast_1d(np.asarray(Q, dtype=np.float64))
+    if f32:
+        k = np.floor(Q.astype(np.float32) * np.float32(n / L)).astype(np.float64)
+    else:
+        k = np.floor(Q / (L / n))
+    k = np.where(np.isfinite(k), k, 0.0)
+    return np.clip(k, 0, n - 1).astype(np.int32)
 
 
 def deposit2d(Qx, Qy, psx, psy, psi, Lx, Ly, nx, ny, cx=None, cy=None):

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libswpic.so")
-SOURCES = ["api.cu", "pass.cu", "sort.cu", "init.cu", "kmeans.cu", "static_deposit.cu"]
+SOURCES = ["api.cu", "pass.cu", "sort.cu", "init.cu", "kmeans.cu", "static_deposit.cu", "api2d.cu", "pass2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 # the particle pass writes its fused multiply-adds out, and the k-means
@@ -38,7 +38,8 @@ def _stale(obj, deps):
 def build(force=False, verbose=False):
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
-    headers = [os.path.join(INCLUDE, "swpic.h"), os.path.join(CSRC, "swpic_internal.cuh")]
+    headers = [os.path.join(INCLUDE, "swpic.h"), os.path.join(CSRC, "swpic_internal.cuh"),
+               os.path.join(INCLUDE, "swpic2d.h"), os.path.join(CSRC, "swpic2d_internal.cuh")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -1,0 +1,413 @@
+// Kernels of the 2D2V decorated-particle step (general-d model of Sec. 3.3 on
+// the torus T^2, bilinear elements, leapfrog of Sec. 5).
+//
+//   k_pass2d      one fused pass over the particles: gather grad phi_h and the
+//                 projected Hessian from the node table in shared memory,
+//                 closing half-kick, diagnostics at the integer time, opening
+//                 half-kick, drift, wrap, deposit of the drifted monopole +
+//                 dipole charge into a per-CTA shared mesh, flush to a global
+//                 64-bit fixed-point accumulator (Eq. swpic_poisson, S_h = delta)
+//   k_rows_fwd    node loads -> FP64, forward DFT of every mesh row
+//   k_cols        per column: forward DFT, divide by the Q1 stiffness symbol
+//                 (zero mode dropped: neutralising background + zero-mean gauge),
+//                 inverse DFT
+//   k_rows_inv    inverse DFT of every row -> Phi, field energy (1/2) Phi^T b
+//   k_table       lumped projection g of grad phi_h, node table (Phi, g) in the
+//                 state precision
+//   k_record      one diagnostic record
+//
+// The DFTs are radix-2 in shared memory, one CTA per row or column, in FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "swpic2d_internal.cuh"
+
+namespace swpic2d {
+
+// node table entry (Phi, g_x, g_y, pad): one 16-byte load (FP32) or two (FP64)
+struct alignas(16) Node64 { double x, y, z, w; };
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = Node64; };
+
+__device__ __forceinline__ float flr(float x) { return floorf(x); }
+__device__ __forceinline__ double flr(double x) { return floor(x); }
+
+// Cell along one axis: floor(Q / h) as one multiply by 1/h in the state
+// precision, clamped to [0, n-1]; frac = Q/h - i (the local coordinate).
+template <typename T>
+__device__ __forceinline__ int cell_of(T Q, T inv_h, int n, T &frac) {
+    const T s = Q * inv_h;
+    const T f = flr(s);
+    const int i = (f >= T(0)) ? ((f < (T)n) ? (int)f : n - 1) : 0;     // NaN -> 0
+    frac = s - (T)i;
+    return i;
+}
+
+// Periodic wrap into [0, L); a value that rounds up to L maps to 0.
+template <typename T>
+__device__ __forceinline__ T wrap(T Q, T L, T inv_L) {
+    if (Q >= T(0) && Q < L) return Q;
+    T w = Q - L * flr(Q * inv_L);
+    if (w >= L) w -= L;
+    if (w < T(0)) w += L;
+    if (w >= L) w = T(0);
+    return w;
+}
+
+template <typename T>
+struct Kahan {
+    T s, c;
+    __device__ __forceinline__ void add(T x) {
+        const T y = x - c;
+        const T t = s + y;
+        c = (t - s) - y;
+        s = t;
+    }
+    __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// FP64 block sum; every thread of the block must call it.  Result valid in thread 0.
+__device__ double block_sum(double v, double *sh) {
+    v = warp_sum(v);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < nw; ++k) s += sh[k];
+    return s;
+}
+
+__device__ __forceinline__ unsigned long long to_fixed(double v, double scale, int *err) {
+    const double x = v * scale;
+    if (!(fabs(x) < 4.611686018427388e18)) {       // 2^62; also catches NaN
+        atomicOr(err, isfinite(v) ? kErrOverflow : kErrNonFinite);
+        return 0ull;
+    }
+    return (unsigned long long)__double2ll_rn(x);
+}
+
+// ---------------------------------------------------------------------------
+// The fused particle pass
+// ---------------------------------------------------------------------------
+template <typename T, bool DEC, bool DEP, bool DIAG>
+__global__ void __launch_bounds__(512) k_pass2d(PassArgs2d a) {
+    using T4 = typename V4<T>::type;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[32];
+    const int nx = a.nx, ny = a.ny, nn = nx * ny;
+    T4 *tab = reinterpret_cast<T4 *>(smem);
+    T *mesh = reinterpret_cast<T *>(smem + (size_t)nn * sizeof(T4));
+    const T4 *gtab = reinterpret_cast<const T4 *>(a.table);
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+        tab[k] = gtab[k];
+        if (DEP) mesh[k] = T(0);
+    }
+    __syncthreads();
+
+    T *Qx = static_cast<T *>(a.Qx), *Qy = static_cast<T *>(a.Qy);
+    T *Px = static_cast<T *>(a.Px), *Py = static_cast<T *>(a.Py);
+    T *qx = static_cast<T *>(a.qx), *qy = static_cast<T *>(a.qy);
+    T *px = static_cast<T *>(a.px), *py = static_cast<T *>(a.py);
+    const T *psi = static_cast<const T *>(a.psi);
+    const T Lx = (T)a.Lx, Ly = (T)a.Ly, iLx = (T)a.inv_Lx, iLy = (T)a.inv_Ly;
+    const T ihx = (T)a.inv_hx, ihy = (T)a.inv_hy;
+    const T k1 = (T)a.k1, k2 = (T)a.k2, kd = (T)a.kd;
+    Kahan<T> s_m{T(0), T(0)}, s_x{T(0), T(0)}, s_y{T(0), T(0)}, s_k{T(0), T(0)};
+
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += stride) {
+        T x = Qx[p], y = Qy[p], vx = Px[p], vy = Py[p];
+        const T w = psi[p];
+        T sx = T(0), sy = T(0), rx = T(0), ry = T(0);     // q*, p*
+        if (DEC) { sx = qx[p]; sy = qy[p]; rx = px[p]; ry = py[p]; }
+        // grad phi_h and H_ik = d_k g_i at Q from the four corners of the cell
+        T xi, eta;
+        const int i = cell_of(x, ihx, nx, xi), j = cell_of(y, ihy, ny, eta);
+        const int i1 = (i + 1 == nx) ? 0 : i + 1, j1 = (j + 1 == ny) ? 0 : j + 1;
+        const T4 c00 = tab[j * nx + i], c10 = tab[j * nx + i1], c01 = tab[j1 * nx + i], c11 = tab[j1 * nx + i1];
+        const T oe = T(1) - eta, ox = T(1) - xi;
+        const T ex = ((c10.x - c00.x) * oe + (c11.x - c01.x) * eta) * ihx;
+        const T ey = ((c01.x - c00.x) * ox + (c11.x - c10.x) * xi) * ihy;
+        T hxx = T(0), hxy = T(0), hyx = T(0), hyy = T(0);
+        if (DEC) {
+            hxx = ((c10.y - c00.y) * oe + (c11.y - c01.y) * eta) * ihx;
+            hxy = ((c01.y - c00.y) * ox + (c11.y - c10.y) * xi) * ihy;
+            hyx = ((c10.z - c00.z) * oe + (c11.z - c01.z) * eta) * ihx;
+            hyy = ((c01.z - c00.z) * ox + (c11.z - c10.z) * xi) * ihy;
+        }
+        // closing half-kick of the previous step
+        vx -= k1 * ex;
+        vy -= k1 * ey;
+        if (DEC) {
+            sx += k1 * (hxx * rx + hxy * ry);
+            sy += k1 * (hyx * rx + hyy * ry);
+        }
+        if (DIAG) {
+            s_m.add(w);
+            s_x.add(w * vx + sx);
+            s_y.add(w * vy + sy);
+            s_k.add(T(0.5) * w * (vx * vx + vy * vy) + (sx * vx + sy * vy));
+        }
+        // opening half-kick of the next step
+        vx -= k2 * ex;
+        vy -= k2 * ey;
+        if (DEC) {
+            sx += k2 * (hxx * rx + hxy * ry);
+            sy += k2 * (hyx * rx + hyy * ry);
+        }
+        // drift
+        x = wrap(x + kd * vx, Lx, iLx);
+        y = wrap(y + kd * vy, Ly, iLy);
+        if (DEC) {
+            rx -= kd * sx;
+            ry -= kd * sy;
+        }
+        Qx[p] = x; Qy[p] = y; Px[p] = vx; Py[p] = vy;
+        if (DEC) { qx[p] = sx; qy[p] = sy; px[p] = rx; py[p] = ry; }
+        if (DEP) {
+            // psi* N_c(Q) - p* . grad N_c(Q) for the four corners
+            T u, v;
+            const int di = cell_of(x, ihx, nx, u), dj = cell_of(y, ihy, ny, v);
+            const int di1 = (di + 1 == nx) ? 0 : di + 1, dj1 = (dj + 1 == ny) ? 0 : dj + 1;
+            const T ou = T(1) - u, ov = T(1) - v;
+            const T ax = DEC ? rx * ihx : T(0), ay = DEC ? ry * ihy : T(0);
+            atomicAdd(mesh + dj * nx + di, w * ou * ov + ax * ov + ay * ou);
+            atomicAdd(mesh + dj * nx + di1, w * u * ov - ax * ov + ay * u);
+            atomicAdd(mesh + dj1 * nx + di, w * ou * v + ax * v - ay * ou);
+            atomicAdd(mesh + dj1 * nx + di1, w * u * v - ax * v - ay * u);
+        }
+    }
+    __syncthreads();
+    if (DEP) {
+        for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+            const T v = mesh[k];
+            if (v != T(0)) atomicAdd(a.acc + k, to_fixed((double)v, a.fx_scale, a.err));
+        }
+    }
+    if (DIAG) {
+        const double m = block_sum(s_m.value(), s_red);
+        const double mx = block_sum(s_x.value(), s_red);
+        const double my = block_sum(s_y.value(), s_red);
+        const double kk = block_sum(s_k.value(), s_red);
+        if (threadIdx.x == 0) {
+            atomicAdd(a.diag_acc + 0, m);
+            atomicAdd(a.diag_acc + 1, mx);
+            atomicAdd(a.diag_acc + 2, my);
+            atomicAdd(a.diag_acc + 3, kk);
+        }
+    }
+}
+
+// Bound of every partial sum of the deposit: sum psi* + 2 sum |p*_x|/hx +
+// 2 sum |p*_y|/hy (FP64 atomics; only its binary exponent is used).
+template <typename T>
+__global__ void __launch_bounds__(256) k_bound2d(PassArgs2d a, double *out) {
+    __shared__ double s_red[32];
+    const T *psi = static_cast<const T *>(a.psi);
+    const T *px = static_cast<const T *>(a.px), *py = static_cast<const T *>(a.py);
+    double s = 0.0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += stride) {
+        s += fabs((double)psi[p]);
+        if (px) s += 2.0 * (fabs((double)px[p]) * a.inv_hx + fabs((double)py[p]) * a.inv_hy);
+    }
+    s = block_sum(s, s_red);
+    if (threadIdx.x == 0) atomicAdd(out, s);
+}
+
+// ---------------------------------------------------------------------------
+// Spectral solve
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int bit_reverse(int i, int logn) {
+    return (logn == 0) ? 0 : (int)(__brev((unsigned)i) >> (32 - logn));
+}
+
+// In-place radix-2 DFT of n = 2^logn points already in bit-reversed order
+// (sign -1 forward, +1 inverse; no normalisation).  All threads call it.
+__device__ void fft_inplace(double2 *z, int n, const double2 *tw, int ntw, bool inverse) {
+    for (int len = 2; len <= n; len <<= 1) {
+        const int half = len >> 1, step = ntw / len;
+        for (int b = threadIdx.x; b < (n >> 1); b += blockDim.x) {
+            const int g = b / half, pos = b - g * half;
+            const int i0 = g * len + pos, i1 = i0 + half;
+            double2 w = tw[pos * step];
+            if (inverse) w.y = -w.y;
+            const double2 u = z[i0], v = z[i1];
+            const double2 t = make_double2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+            z[i0] = make_double2(u.x + t.x, u.y + t.y);
+            z[i1] = make_double2(u.x - t.x, u.y - t.y);
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(256) k_rows_fwd(SolveArgs2d s) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double2 *z = reinterpret_cast<double2 *>(smem);
+    const int j = blockIdx.x, nx = s.nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const int k = j * nx + i;
+        const long long q = (long long)s.acc[k];
+        s.acc[k] = 0ull;
+        const double b = (double)q * s.fx_inv;
+        s.b[k] = b;
+        z[bit_reverse(i, s.lognx)] = make_double2(b, 0.0);
+    }
+    if (j == 0 && threadIdx.x == 0) *s.W = 0.0;
+    __syncthreads();
+    fft_inplace(z, nx, s.tw, s.ntw, false);
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) s.spec[j * nx + i] = z[i];
+}
+
+__global__ void __launch_bounds__(256) k_cols(SolveArgs2d s) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ny = s.ny, nx = s.nx, kx = blockIdx.x;
+    double2 *z = reinterpret_cast<double2 *>(smem), *y = z + ny;
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) z[bit_reverse(j, s.logny)] = s.spec[j * nx + kx];
+    __syncthreads();
+    fft_inplace(z, ny, s.tw, s.ntw, false);
+    for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
+        const double il = s.inv_lam[ky * nx + kx];
+        const double2 v = z[ky];
+        y[bit_reverse(ky, s.logny)] = make_double2(v.x * il, v.y * il);
+    }
+    __syncthreads();
+    fft_inplace(y, ny, s.tw, s.ntw, true);
+    for (int j = threadIdx.x; j < ny; j += blockDim.x) s.spec[j * nx + kx] = y[j];
+}
+
+__global__ void __launch_bounds__(256) k_rows_inv(SolveArgs2d s) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ double s_red[32];
+    double2 *z = reinterpret_cast<double2 *>(smem);
+    const int j = blockIdx.x, nx = s.nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) z[bit_reverse(i, s.lognx)] = s.spec[j * nx + i];
+    __syncthreads();
+    fft_inplace(z, nx, s.tw, s.ntw, true);
+    double e = 0.0;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+        const double phi = z[i].x * s.inv_nn;
+        s.phi[j * nx + i] = phi;
+        e += phi * s.b[j * nx + i];
+    }
+    e = block_sum(e, s_red);
+    if (threadIdx.x == 0) {
+        atomicAdd(s.W, 0.5 * e);
+        if (!isfinite(e)) atomicOr(s.err, kErrNonFinite);
+    }
+}
+
+// g_x(i,j) = (2/3) C_x(i,j) + (1/6)(C_x(i,j-1) + C_x(i,j+1)), C_x the central
+// difference of Phi along x (the lumped projection of grad phi_h on a uniform
+// bilinear mesh); g_y likewise across.
+template <typename T>
+__global__ void __launch_bounds__(256) k_table2d(SolveArgs2d s) {
+    using T4 = typename V4<T>::type;
+    const int nx = s.nx, ny = s.ny;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nx * ny) return;
+    const int i = k % nx, j = k / nx;
+    const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
+    const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
+    const double *P = s.phi;
+    auto cx = [&](int r) { return (P[r * nx + ip] - P[r * nx + im]) * (0.5 * s.inv_hx); };
+    auto cy = [&](int c) { return (P[jp * nx + c] - P[jm * nx + c]) * (0.5 * s.inv_hy); };
+    const double gx = (2.0 / 3.0) * cx(j) + (1.0 / 6.0) * (cx(jm) + cx(jp));
+    const double gy = (2.0 / 3.0) * cy(i) + (1.0 / 6.0) * (cy(im) + cy(ip));
+    T4 t;
+    t.x = (T)P[k];
+    t.y = (T)gx;
+    t.z = (T)gy;
+    t.w = T(0);
+    reinterpret_cast<T4 *>(s.table)[k] = t;
+}
+
+__global__ void k_record2d(RecordArgs2d r) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    const double W = *r.W;
+    double *o = r.rec;
+    o[0] = r.t;
+    o[1] = r.diag_acc[0];
+    o[2] = r.diag_acc[1];
+    o[3] = r.diag_acc[2];
+    o[4] = r.diag_acc[3];
+    o[5] = W;
+    o[6] = r.diag_acc[3] + W;
+    o[7] = sqrt(fmax(2.0 * W / r.area, 0.0));
+    o[8] = (double)r.step;
+    if (!isfinite(o[6])) atomicOr(r.err, kErrNonFinite);
+    for (int q = 0; q < 4; ++q) r.diag_acc[q] = 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+size_t pass_smem_bytes(int prec, int nn, bool deposit) {
+    const size_t e = (prec == SWPIC_F64) ? 8 : 4;
+    return (size_t)nn * 4 * e + (deposit ? (size_t)nn * e : 0);
+}
+
+template <typename T>
+static const void *pass_kernel_t(bool dec, bool dep, bool diag) {
+    const int c = (dec ? 4 : 0) | (dep ? 2 : 0) | (diag ? 1 : 0);
+    switch (c) {
+    case 0: return (const void *)k_pass2d<T, false, false, false>;
+    case 1: return (const void *)k_pass2d<T, false, false, true>;
+    case 2: return (const void *)k_pass2d<T, false, true, false>;
+    case 3: return (const void *)k_pass2d<T, false, true, true>;
+    case 4: return (const void *)k_pass2d<T, true, false, false>;
+    case 5: return (const void *)k_pass2d<T, true, false, true>;
+    case 6: return (const void *)k_pass2d<T, true, true, false>;
+    default: return (const void *)k_pass2d<T, true, true, true>;
+    }
+}
+
+const void *pass_kernel(int prec, bool decorated, bool deposit, bool diag) {
+    return prec == SWPIC_F64 ? pass_kernel_t<double>(decorated, deposit, diag)
+                             : pass_kernel_t<float>(decorated, deposit, diag);
+}
+
+cudaError_t launch_pass(int prec, bool decorated, bool deposit, bool diag, const PassArgs2d &a, int grid,
+                        int tpb, size_t smem, cudaStream_t s) {
+    const void *fn = pass_kernel(prec, decorated, deposit, diag);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    PassArgs2d copy = a;
+    void *args[] = {&copy};
+    return cudaLaunchKernel(fn, dim3(grid), dim3(tpb), args, smem, s);
+}
+
+cudaError_t launch_bound(int prec, const PassArgs2d &a, double *out, int grid, cudaStream_t s) {
+    if (prec == SWPIC_F64) k_bound2d<double><<<grid, 256, 0, s>>>(a, out);
+    else k_bound2d<float><<<grid, 256, 0, s>>>(a, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_solve(int prec, const SolveArgs2d &a, cudaStream_t s, int64_t *launches) {
+    const int tr = a.nx >= 256 ? 256 : (a.nx >= 64 ? a.nx / 2 : 32);
+    const int tc = a.ny >= 256 ? 256 : (a.ny >= 64 ? a.ny / 2 : 32);
+    k_rows_fwd<<<a.ny, tr, (size_t)a.nx * sizeof(double2), s>>>(a);
+    k_cols<<<a.nx, tc, (size_t)2 * a.ny * sizeof(double2), s>>>(a);
+    k_rows_inv<<<a.ny, tr, (size_t)a.nx * sizeof(double2), s>>>(a);
+    const int nn = a.nx * a.ny;
+    if (prec == SWPIC_F64) k_table2d<double><<<(nn + 255) / 256, 256, 0, s>>>(a);
+    else k_table2d<float><<<(nn + 255) / 256, 256, 0, s>>>(a);
+    *launches += 4;
+    return cudaGetLastError();
+}
+
+cudaError_t launch_record(const RecordArgs2d &a, cudaStream_t s) {
+    k_record2d<<<1, 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace swpic2d

@@ -49,6 +49,19 @@ class swpic_lattice(C.Structure):
                 ("decorate", C.c_int32), ("reserved", C.c_int32)]
 
 
+class swpic2d_config(C.Structure):
+    _fields_ = [("Lx", C.c_double), ("Ly", C.c_double), ("dt", C.c_double), ("nx", C.c_int32),
+                ("ny", C.c_int32), ("precision", C.c_int32), ("decorated", C.c_int32),
+                ("threads_per_block", C.c_int32), ("blocks_per_sm", C.c_int32),
+                ("diag_capacity", C.c_int32), ("reserved", C.c_int32)]
+
+
+class swpic2d_diag(C.Structure):
+    _fields_ = [("t", C.c_double), ("mass", C.c_double), ("momentum_x", C.c_double),
+                ("momentum_y", C.c_double), ("kinetic", C.c_double), ("field_energy", C.c_double),
+                ("hamiltonian", C.c_double), ("e_amp", C.c_double), ("step", C.c_int64)]
+
+
 _P = C.c_void_p
 _D = C.POINTER(C.c_double)
 _CTX = C.c_void_p
@@ -95,6 +108,19 @@ SIGNATURES = {
     "swpic_set_timing": (C.c_int, [_CTX, C.c_int32]),
     "swpic_pass_times": (C.c_int, [_CTX, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
     "swpic_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
+    # include/swpic2d.h
+    "swpic2d_create": (C.c_int, [C.POINTER(swpic2d_config), C.c_int64, C.POINTER(_CTX)]),
+    "swpic2d_destroy": (None, [_CTX]),
+    "swpic2d_last_error": (C.c_char_p, [_CTX]),
+    "swpic2d_bind_state": (C.c_int, [_CTX, C.POINTER(_P), _P]),
+    "swpic2d_refresh": (C.c_int, [_CTX]),
+    "swpic2d_step": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
+    "swpic2d_diagnostics": (C.c_int, [_CTX, C.POINTER(swpic2d_diag), C.c_int32, C.POINTER(C.c_int32)]),
+    "swpic2d_get_field": (C.c_int, [_CTX, _D, _D, _D, _D]),
+    "swpic2d_synchronize": (C.c_int, [_CTX]),
+    "swpic2d_set_timing": (C.c_int, [_CTX, C.c_int32]),
+    "swpic2d_pass_times": (C.c_int, [_CTX, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
+    "swpic2d_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
 }
 
 _lib = None
@@ -124,10 +150,10 @@ class SwpicError(RuntimeError):
         self.status = status
 
 
-def _check(st, ctx=None):
+def _check(st, ctx=None, last_error="swpic_last_error"):
     if st != SWPIC_OK:
         lib = load_library()
-        msg = lib.swpic_last_error(ctx).decode() if ctx else ""
+        msg = getattr(lib, last_error)(ctx).decode() if ctx else ""
         raise SwpicError(st, "%s: %s" % (lib.swpic_status_string(st).decode(), msg))
 
 
@@ -419,3 +445,142 @@ class Simulation:
 
     def mesh(self, run=0):
         return swpic_get_mesh(self.ctx, run, self.runs[run][2])
+
+
+# ---------------------------------------------------------------------------
+# 2D2V (include/swpic2d.h): same-name wrappers
+# ---------------------------------------------------------------------------
+STATE2D = ("Qx", "Qy", "Px", "Py", "qx", "qy", "px", "py", "psi")
+
+
+def _check2(st, ctx=None):
+    _check(st, ctx, "swpic2d_last_error")
+
+
+def swpic2d_create(cfg: swpic2d_config, n_particles: int):
+    ctx = _CTX()
+    _check2(load_library().swpic2d_create(C.byref(cfg), int(n_particles), C.byref(ctx)))
+    return ctx
+
+
+def swpic2d_destroy(ctx):
+    load_library().swpic2d_destroy(ctx)
+
+
+def swpic2d_last_error(ctx):
+    return load_library().swpic2d_last_error(ctx).decode()
+
+
+def swpic2d_bind_state(ctx, ptrs, stream):
+    arr = (_P * 9)(*[None if p is None else int(p) for p in ptrs])
+    _check2(load_library().swpic2d_bind_state(ctx, arr, stream), ctx)
+
+
+def swpic2d_refresh(ctx):
+    _check2(load_library().swpic2d_refresh(ctx), ctx)
+
+
+def swpic2d_step(ctx, n_steps, diag_every=0):
+    _check2(load_library().swpic2d_step(ctx, int(n_steps), int(diag_every)), ctx)
+
+
+def swpic2d_diagnostics(ctx, max_records=100000):
+    """(n, 9) array: t, mass, momentum_x, momentum_y, kinetic, field_energy,
+    hamiltonian, e_amp, step."""
+    buf = (swpic2d_diag * max_records)()
+    n = C.c_int32(0)
+    _check2(load_library().swpic2d_diagnostics(ctx, buf, int(max_records), C.byref(n)), ctx)
+    out = np.zeros((n.value, 9))
+    for k in range(n.value):
+        d = buf[k]
+        out[k] = [d.t, d.mass, d.momentum_x, d.momentum_y, d.kinetic, d.field_energy, d.hamiltonian,
+                  d.e_amp, d.step]
+    return out
+
+
+def swpic2d_get_field(ctx, nx, ny):
+    arrs = {k: np.zeros((ny, nx)) for k in ("b", "Phi", "gx", "gy")}
+    _check2(load_library().swpic2d_get_field(ctx, *[_dptr(arrs[k]) for k in ("b", "Phi", "gx", "gy")]), ctx)
+    return arrs
+
+
+def swpic2d_synchronize(ctx):
+    _check2(load_library().swpic2d_synchronize(ctx), ctx)
+
+
+def swpic2d_set_timing(ctx, enable):
+    _check2(load_library().swpic2d_set_timing(ctx, int(bool(enable))), ctx)
+
+
+def swpic2d_pass_times(ctx, max_passes=100000):
+    buf = (C.c_float * max_passes)()
+    n = C.c_int32(0)
+    _check2(load_library().swpic2d_pass_times(ctx, buf, int(max_passes), C.byref(n)), ctx)
+    return np.array(buf[: n.value], dtype=np.float64)
+
+
+def swpic2d_launch_count(ctx):
+    n = C.c_int64(0)
+    _check2(load_library().swpic2d_launch_count(ctx, C.byref(n)), ctx)
+    return n.value
+
+
+class Simulation2D:
+    """Owns the nine particle tensors (torch, cuda) of one 2D2V run and a
+    context bound to them."""
+
+    def __init__(self, Lx, Ly, nx, ny, dt, n, precision=32, decorated=True, threads_per_block=0,
+                 blocks_per_sm=0, diag_capacity=0, stream=None, device="cuda"):
+        import torch
+        self.torch = torch
+        self.nx, self.ny, self.n = int(nx), int(ny), int(n)
+        self.decorated = decorated
+        self.dtype = torch.float64 if precision == 64 else torch.float32
+        cfg = swpic2d_config(float(Lx), float(Ly), float(dt), int(nx), int(ny), int(precision),
+                             int(bool(decorated)), int(threads_per_block), int(blocks_per_sm),
+                             int(diag_capacity), 0)
+        self.ctx = swpic2d_create(cfg, self.n)
+        m = max(self.n, 1)
+        self.t = {k: (torch.zeros(m, dtype=self.dtype, device=device)
+                      if decorated or k not in ("qx", "qy", "px", "py") else None) for k in STATE2D}
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        swpic2d_bind_state(self.ctx, [None if v is None else v.data_ptr() for v in self.t.values()],
+                           self.stream.cuda_stream)
+
+    def close(self):
+        if self.ctx:
+            swpic2d_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init_particles(self, state):
+        """Copy a host state (dict of FP64 arrays with the STATE2D keys) into the
+        device tensors and take its field (swpic2d_refresh)."""
+        torch = self.torch
+        torch.cuda.synchronize()
+        for k, v in self.t.items():
+            if v is None:
+                continue
+            src = state.get(k)
+            src = np.zeros(self.n) if src is None else np.asarray(src, dtype=np.float64)
+            v[: self.n].copy_(torch.from_numpy(np.ascontiguousarray(src)).to(self.dtype))
+        torch.cuda.synchronize()
+        swpic2d_refresh(self.ctx)
+
+    def state(self):
+        swpic2d_synchronize(self.ctx)
+        return {k: (None if v is None else v[: self.n].double().cpu().numpy()) for k, v in self.t.items()}
+
+    def step(self, n, diag_every=0):
+        swpic2d_step(self.ctx, n, diag_every)
+
+    def diagnostics(self):
+        return swpic2d_diagnostics(self.ctx)
+
+    def field(self):
+        return swpic2d_get_field(self.ctx, self.nx, self.ny)

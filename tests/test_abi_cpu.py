@@ -11,13 +11,15 @@ import tempfile
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "swpic.h")
+HEADERS = [os.path.join(ROOT, "include", h) for h in ("swpic.h", "swpic2d.h")]
 
 
 def declared_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(swpic_[a-z_0-9]+)\s*\(", text)))
+    names = set()
+    for h in HEADERS:
+        text = re.sub(r"/\*.*?\*/", "", open(h).read(), flags=re.S)
+        names |= set(re.findall(r"\b(swpic(?:2d)?_[a-z_0-9]+)\s*\(", text))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +40,7 @@ def test_library_exports_every_declared_function(lib):
     out = subprocess.run(["nm", "-D", "--defined-only",
                           os.path.join(ROOT, "paper_2605_21794_gb300", "_build", "libswpic.so")],
                          capture_output=True, text=True, check=True).stdout
-    exported = set(re.findall(r"\sT\s(swpic_[a-z_0-9]+)$", out, flags=re.M))
+    exported = set(re.findall(r"\sT\s(swpic(?:2d)?_[a-z_0-9]+)$", out, flags=re.M))
     missing = [n for n in declared_functions() if n not in exported]
     assert not missing, missing
     for n in declared_functions():
@@ -104,3 +106,43 @@ def test_null_context_is_rejected(lib):
     assert lib.swpic_step(None, 1, 0) == swpic.SWPIC_EINVAL
     assert lib.swpic_deposit(None) == swpic.SWPIC_EINVAL
     lib.swpic_destroy(None)
+
+
+def test_2d_struct_layouts_match_c(tmp_path):
+    from paper_2605_21794_gb300 import swpic
+    src = tmp_path / "layout2d.c"
+    src.write_text('''
+#include <stdio.h>
+#include <stddef.h>
+#include "swpic2d.h"
+int main(void) {
+  printf("%zu %zu %zu %zu\\n", sizeof(swpic2d_config), sizeof(swpic2d_diag),
+         offsetof(swpic2d_config, diag_capacity), offsetof(swpic2d_diag, step));
+  return 0;
+}''')
+    exe = tmp_path / "layout2d"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True,
+                                          check=True).stdout.split()]
+    assert got == [C.sizeof(swpic.swpic2d_config), C.sizeof(swpic.swpic2d_diag),
+                   swpic.swpic2d_config.diag_capacity.offset, swpic.swpic2d_diag.step.offset]
+
+
+def test_2d_create_rejects_bad_configs_before_touching_the_device(lib):
+    from paper_2605_21794_gb300 import swpic
+    ctx = swpic._CTX()
+
+    def cfg(**kw):
+        base = dict(Lx=1.0, Ly=1.0, dt=0.1, nx=16, ny=16, precision=32, decorated=1,
+                    threads_per_block=0, blocks_per_sm=0, diag_capacity=0, reserved=0)
+        base.update(kw)
+        return swpic.swpic2d_config(*base.values())
+    bad = [cfg(Lx=-1.0), cfg(Ly=0.0), cfg(dt=0.0), cfg(nx=12), cfg(ny=2), cfg(nx=2048),
+           cfg(nx=128, ny=128), cfg(precision=64, nx=128, ny=64), cfg(precision=16),
+           cfg(threads_per_block=100), cfg(threads_per_block=1024), cfg(diag_capacity=-1)]
+    for c in bad:
+        assert lib.swpic2d_create(C.byref(c), 10, C.byref(ctx)) == swpic.SWPIC_EINVAL
+    assert lib.swpic2d_create(C.byref(cfg()), -1, C.byref(ctx)) == swpic.SWPIC_EINVAL
+    assert lib.swpic2d_step(None, 1, 0) == swpic.SWPIC_EINVAL
+    assert lib.swpic2d_refresh(None) == swpic.SWPIC_EINVAL
+    lib.swpic2d_destroy(None)

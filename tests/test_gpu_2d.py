@@ -1,0 +1,179 @@
+"""GPU parity of the 2D2V decorated-particle step (general-d model of Sec. 3.3
+on the torus, bilinear elements) against the 2D oracle, through the C ABI
+of include/swpic2d.h.
+
+The kernels solve the Q1 system by the discrete Fourier transform (the
+stiffness is diagonal in Fourier modes) and take the projected gradient from
+its closed form; the oracle assembles the stiffness by quadrature, solves
+the bordered system by LU and projects by quadrature.  FP64: the field
+(b, Phi, g) within 1e-12 of the oracle's, every state array within 1e-12
+after one step, diagnostics within 1e-11, several steps within 1e-10.  FP32:
+the oracle keeps FP32 storage and FP32 cell decisions; 1e-5.  Also: a call
+of n steps equals n calls of one step bit for bit (the closing and opening
+half-kicks of the fused pass are the same two operations), an empty run,
+invalid calls, and the workload size at the property level.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import workloads as W
+from gpu_util import need_gpu, periodic_diff, rel_max
+
+pytestmark = pytest.mark.gpu
+KEYS = ("Qx", "Qy", "Px", "Py", "qx", "qy", "px", "py")
+
+
+def _sim(Lx, Ly, nx, ny, dt, n, precision, **kw):
+    from paper_2605_21794_gb300 import swpic
+    return swpic.Simulation2D(Lx, Ly, nx, ny, dt, n, precision=precision, **kw)
+
+
+def _cast(st, precision):
+    dt = np.float32 if precision == 32 else np.float64
+    return {k: (None if v is None else np.asarray(v).astype(dt).astype(np.float64)) for k, v in st.items()}
+
+
+def _compare(got, ref, Lx, Ly, tol, keys=KEYS):
+    for k in keys:
+        if ref.get(k) is None or got.get(k) is None:
+            continue
+        if k in ("Qx", "Qy"):
+            L = Lx if k == "Qx" else Ly
+            err = np.abs(periodic_diff(got[k], ref[k], L)).max() / L
+        else:
+            err = rel_max(got[k], ref[k])
+        assert err <= tol, (k, err)
+
+
+def _run(precision, st, Lx, Ly, nx, ny, dt, steps, diag_every=1, decorated=True, calls=None):
+    sim = _sim(Lx, Ly, nx, ny, dt, len(st["Qx"]), precision, decorated=decorated)
+    try:
+        sim.init_particles(st)
+        for k in (calls or [steps]):
+            sim.step(k, diag_every)
+        return sim.state(), sim.diagnostics(), sim.field()
+    finally:
+        sim.close()
+
+
+@pytest.mark.parametrize("decorated", [True, False])
+def test_field_of_a_state_matches_oracle_fp64(decorated):
+    need_gpu()
+    Lx, Ly, nx, ny = 4 * np.pi, 2 * np.pi, 32, 16
+    st = W.random_state_2d(6000, Lx, Ly, seed=3, nx=nx, ny=ny, decorated=decorated)
+    sim = _sim(Lx, Ly, nx, ny, 0.1, 6000, 64, decorated=decorated)
+    try:
+        sim.init_particles(st)
+        f = sim.field()
+    finally:
+        sim.close()
+    b = O.deposit2d(st["Qx"], st["Qy"], st["px"] if decorated else None, st["py"], st["psi"], Lx, Ly, nx, ny)
+    Phi, _ = O.solve2d(b, Lx, Ly)
+    gx, gy = O.project2d(Phi, Lx, Ly)
+    assert rel_max(f["b"], b) < 1e-12
+    assert rel_max(f["Phi"], Phi) < 1e-12
+    assert rel_max(f["gx"], gx) < 1e-12
+    assert rel_max(f["gy"], gy) < 1e-12
+
+
+@pytest.mark.parametrize("decorated", [True, False])
+def test_one_fp64_step_matches_oracle(decorated):
+    need_gpu()
+    Lx, Ly, nx, ny, dt = 4 * np.pi, 4 * np.pi, 16, 16, 0.1
+    st = W.random_state_2d(4096, Lx, Ly, seed=11, nx=nx, ny=ny, decorated=decorated)
+    got, diag, _ = _run(64, st, Lx, Ly, nx, ny, dt, 1, decorated=decorated)
+    ref = O.run2d(st, nx, ny, Lx, Ly, dt, 1, diag_every=1, decorated=decorated)
+    _compare(got, ref, Lx, Ly, 1e-12, KEYS if decorated else KEYS[:4])
+    assert diag.shape == (2, 9)
+    np.testing.assert_allclose(diag[:, 0], [0.0, dt])
+    np.testing.assert_array_equal(diag[:, 8], [0, 1])
+    for c in range(1, 8):
+        assert rel_max(diag[:, c], ref["diag"][:, c]) < 1e-11, c
+
+
+def test_several_fp64_steps_non_square_mesh_ragged_count():
+    need_gpu()
+    Lx, Ly, nx, ny, dt = 6.0, 2.5, 32, 8, 0.05
+    st = W.random_state_2d(1031, Lx, Ly, seed=12, nx=nx, ny=ny, alpha=0.3)
+    got, diag, _ = _run(64, st, Lx, Ly, nx, ny, dt, 6, diag_every=2)
+    ref = O.run2d(st, nx, ny, Lx, Ly, dt, 6, diag_every=2)
+    _compare(got, ref, Lx, Ly, 1e-10)
+    assert diag.shape[0] == ref["diag"].shape[0] == 4
+    for c in range(1, 8):
+        assert rel_max(diag[:, c], ref["diag"][:, c]) < 1e-10, c
+
+
+def test_one_fp32_step_matches_fp32_oracle():
+    need_gpu()
+    Lx, Ly, nx, ny, dt = 4 * np.pi, 2 * np.pi, 32, 16, 0.1
+    st = _cast(W.random_state_2d(20000, Lx, Ly, seed=13, nx=nx, ny=ny, alpha=0.2), 32)
+    got, diag, _ = _run(32, st, Lx, Ly, nx, ny, dt, 1)
+    ref = O.run2d(st, nx, ny, Lx, Ly, dt, 1, diag_every=1, store_f32=True)
+    _compare(got, ref, Lx, Ly, 1e-5)
+    for c in (1, 2, 3, 4, 5, 7):
+        assert rel_max(diag[:, c], ref["diag"][:, c]) < 1e-5, c
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_n_steps_in_one_call_equal_n_calls_bitwise(precision):
+    need_gpu()
+    Lx, Ly, nx, ny, dt = 5.0, 5.0, 16, 32, 0.08
+    st = _cast(W.random_state_2d(3000, Lx, Ly, seed=14, nx=nx, ny=ny), precision)
+    a, da, fa = _run(precision, st, Lx, Ly, nx, ny, dt, 4, diag_every=1)
+    b, db, fb = _run(precision, st, Lx, Ly, nx, ny, dt, 4, diag_every=1, calls=[1, 1, 2])
+    for k in KEYS:
+        assert np.array_equal(a[k], b[k]), k
+    np.testing.assert_array_equal(da[:, 8], np.arange(5))
+    np.testing.assert_array_equal(db[:, 8], np.arange(5))
+    assert np.array_equal(fa["Phi"], fb["Phi"])
+
+
+def test_empty_run_and_invalid_calls():
+    need_gpu()
+    from paper_2605_21794_gb300 import swpic
+    sim = _sim(1.0, 1.0, 8, 8, 0.1, 0, 32)
+    try:
+        sim.init_particles({k: np.zeros(0) for k in swpic.STATE2D})
+        sim.step(3, 1)
+        d = sim.diagnostics()
+        assert d.shape == (4, 9) and np.all(d[:, 1:8] == 0.0)
+        with pytest.raises(swpic.SwpicError):
+            swpic.swpic2d_step(sim.ctx, -1, 0)
+    finally:
+        sim.close()
+    sim = _sim(1.0, 1.0, 8, 8, 0.1, 10, 32)
+    try:
+        with pytest.raises(swpic.SwpicError) as e:        # no refresh after binding
+            swpic.swpic2d_step(sim.ctx, 1, 0)
+        assert e.value.status == swpic.SWPIC_ESTATE
+    finally:
+        sim.close()
+
+
+def test_workload_size_properties():
+    """16,777,216 FP32 particles on a 32 x 32 mesh (the 2D benchmark's size):
+    the field of the state against the oracle's (FP32 cell decisions), mass
+    and charge conservation over steps, the diagnostics finite."""
+    need_gpu()
+    n, Lx, Ly, nx, ny, dt = 1 << 24, 4 * np.pi, 4 * np.pi, 32, 32, 0.1
+    st = _cast(W.random_state_2d(n, Lx, Ly, seed=15, nx=nx, ny=ny, alpha=0.1), 32)
+    sim = _sim(Lx, Ly, nx, ny, dt, n, 32)
+    try:
+        sim.init_particles(st)
+        f0 = sim.field()
+        sim.step(5, 1)
+        f1 = sim.field()
+        d = sim.diagnostics()
+    finally:
+        sim.close()
+    cx = O.cell2d(st["Qx"], Lx, nx, f32=True)
+    cy = O.cell2d(st["Qy"], Ly, ny, f32=True)
+    b = O.deposit2d(st["Qx"], st["Qy"], st["px"], st["py"], st["psi"], Lx, Ly, nx, ny, cx=cx, cy=cy)
+    assert rel_max(f0["b"], b) < 1e-5
+    Phi, _ = O.solve2d(b, Lx, Ly)
+    assert rel_max(f0["Phi"], Phi) < 1e-4
+    total = st["psi"].sum()
+    assert f1["b"].sum() == pytest.approx(total, rel=1e-6)
+    assert np.all(np.isfinite(d)) and d.shape[0] == 6
+    np.testing.assert_allclose(d[:, 1], total, rtol=1e-6)

@@ -207,6 +207,8 @@ def test_fp32_cell_decision():
     h = L / n
     Q = np.array([0.0, h, 3 * h, L - 1e-7, np.nextafter(np.float32(L), 0)], dtype=np.float64)
     got = O.cell2d(Q, L, n, f32=True)
+    assert [O.lib().or2d_cell_f32(float(x), L, n) for x in Q] == list(got)
+    assert [O.lib().or2d_cell(float(x), L, n) for x in Q] == list(O.cell2d(Q, L, n))
     q = Q.astype(np.float32)
     ref = np.clip(np.floor(q * np.float32(n / L)), 0, n - 1).astype(np.int32)
     np.testing.assert_array_equal(got, ref)
