@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--side", type=int, default=4096, help="lattice side (4096 = the workload)")
     ap.add_argument("--launch", default=None, help="TPBxBPSM: fixed launch shape (no autotune)")
     ap.add_argument("--stages", type=int, default=None, help="bulk-copy stages (0 = register loads; no autotune)")
+    ap.add_argument("--only-2d", action="store_true",
+                    help="run only the 2D2V leg (K timed steps) and print its JSON object")
+    ap.add_argument("--side-2d", type=int, default=4096,
+                    help="2D leg: particles = side^2 (4096 = the 2D workload)")
     ap.add_argument("--d2-mode", choices=list(D2_MODES), default="lumped",
                     help="phi'' of the kick: P1 field with a lumped or nodal projection, or the P2 field")
     return ap.parse_args()
@@ -227,6 +231,12 @@ def main():
     import torch
     world, rank, local = dist_env()
     torch.cuda.set_device(local)
+    if args.only_2d:
+        from paper_2605_21794_gb300 import build, swpic
+        build.build()
+        if rank == 0:
+            print(json.dumps(two_d_leg(torch, swpic, args)), flush=True)
+        return
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -518,7 +528,7 @@ def two_d_leg(torch, swpic, args):
     elements): 16,777,216 FP32 decorated particles of a seeded 2D Landau-like
     state on a 32 x 32 mesh of [0, 4 pi)^2, dt 0.1, diagnostics every step;
     warm-up W steps, K device-timed steps, then the per-pass roofline."""
-    n, L, nx, dt = 1 << 24, 4 * np.pi, 32, 0.1
+    n, L, nx, dt = args.side_2d * args.side_2d, 4 * np.pi, 32, 0.1
     st = W.random_state_2d(n, L, L, seed=2024, nx=nx, ny=nx, alpha=0.1)
     sim = swpic.Simulation2D(L, L, nx, nx, dt, n, precision=32, diag_capacity=args.warmup + 2 * args.steps + 8)
     try:
@@ -549,7 +559,7 @@ def two_d_leg(torch, swpic, args):
     peak, peak_src = measured_peak()
     achieved = bpp * n / (avg / 1e3) / 1e9
     H = d[:, 6]
-    return {"workload": "landau2d_random_16M_32x32", "particles": n, "mesh": [nx, nx], "dt": dt,
+    return {"workload": "landau2d_random_%dx%d_mesh_32x32" % (args.side_2d, args.side_2d), "particles": n, "mesh": [nx, nx], "dt": dt,
             "value": n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -9,9 +9,10 @@ the bordered system by LU and projects by quadrature.  FP64: the field
 (b, Phi, g) within 1e-12 of the oracle's, every state array within 1e-12
 after one step, diagnostics within 1e-11, several steps within 1e-10.  FP32:
 the oracle keeps FP32 storage and FP32 cell decisions; 1e-5.  Also: a call
-of n steps equals n calls of one step bit for bit (the closing and opening
-half-kicks of the fused pass are the same two operations), an empty run,
-invalid calls, and the workload size at the property level.
+of n steps equals n calls of one step (the closing and opening half-kicks of
+the fused pass are the same two operations) up to the order of the deposit's
+shared-memory sums, an empty run, invalid calls, and the workload size at
+the property level.
 """
 import numpy as np
 import pytest
@@ -116,17 +117,20 @@ def test_one_fp32_step_matches_fp32_oracle():
 
 
 @pytest.mark.parametrize("precision", [32, 64])
-def test_n_steps_in_one_call_equal_n_calls_bitwise(precision):
+def test_n_steps_in_one_call_equal_n_calls(precision):
+    """Same operations either way; the per-CTA shared-memory sums of the
+    deposit meet in an order the hardware picks, so the two agree to the
+    rounding of those sums, not bit for bit."""
     need_gpu()
     Lx, Ly, nx, ny, dt = 5.0, 5.0, 16, 32, 0.08
     st = _cast(W.random_state_2d(3000, Lx, Ly, seed=14, nx=nx, ny=ny), precision)
     a, da, fa = _run(precision, st, Lx, Ly, nx, ny, dt, 4, diag_every=1)
     b, db, fb = _run(precision, st, Lx, Ly, nx, ny, dt, 4, diag_every=1, calls=[1, 1, 2])
-    for k in KEYS:
-        assert np.array_equal(a[k], b[k]), k
+    tol = 1e-5 if precision == 32 else 1e-12
+    _compare(a, b, Lx, Ly, tol)
     np.testing.assert_array_equal(da[:, 8], np.arange(5))
     np.testing.assert_array_equal(db[:, 8], np.arange(5))
-    assert np.array_equal(fa["Phi"], fb["Phi"])
+    assert rel_max(fa["Phi"], fb["Phi"]) < tol
 
 
 def test_empty_run_and_invalid_calls():
