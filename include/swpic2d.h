@@ -49,7 +49,7 @@ typedef struct swpic2d_config {
     int32_t nx, ny;            /* cells per axis: powers of two in [4, SWPIC2D_N_MAX]    */
     int32_t precision;         /* SWPIC_F32 or SWPIC_F64 (state, push and deposit)      */
     int32_t decorated;         /* 1: monopole + dipole; 0: point-particle PIC            */
-    int32_t threads_per_block; /* 0 = default (256); 64..1024, multiple of 32            */
+    int32_t threads_per_block; /* 0 = default (256); 64..256, multiple of 32             */
     int32_t blocks_per_sm;     /* 0 = default (as many as the shared memory allows, <= 8) */
     int32_t diag_capacity;     /* diagnostic records kept (0 = 4096); later ones dropped  */
     int32_t reserved;

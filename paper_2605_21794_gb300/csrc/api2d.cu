@@ -169,7 +169,7 @@ swpic_status swpic2d_create(const swpic2d_config *cfg, int64_t n_particles, swpi
     if (c.precision != SWPIC_F32 && c.precision != SWPIC_F64) return SWPIC_EINVAL;
     const int nn = c.nx * c.ny;
     if (nn > (c.precision == SWPIC_F64 ? SWPIC2D_NODES_MAX_F64 : SWPIC2D_NODES_MAX_F32)) return SWPIC_EINVAL;
-    if (c.threads_per_block != 0 && (c.threads_per_block < 64 || c.threads_per_block > 512 ||
+    if (c.threads_per_block != 0 && (c.threads_per_block < 64 || c.threads_per_block > 256 ||
                                      c.threads_per_block % 32))
         return SWPIC_EINVAL;
     if (c.blocks_per_sm < 0 || c.blocks_per_sm > 32 || c.diag_capacity < 0) return SWPIC_EINVAL;

@@ -33,14 +33,31 @@ template <> struct V4<double> { using type = Node64; };
 __device__ __forceinline__ float flr(float x) { return floorf(x); }
 __device__ __forceinline__ double flr(double x) { return floor(x); }
 
+// floor(c) and its integer for c = s clamped to [0, cmax], cmax = n - 1/2,
+// without a float <-> int conversion instruction (they run on this GPU's
+// narrow FP64/conversion pipe): adding 2^23 (2^52) rounding down leaves
+// floor(c) in the low mantissa bits.  NaN clamps to 0.
+__device__ __forceinline__ int cell_index(float s, float cmax, float &fi) {
+    const float c = fminf(fmaxf(s, 0.0f), cmax);
+    const float y = __fadd_rd(c, 8388608.0f);
+    fi = y - 8388608.0f;
+    return __float_as_int(y) - 0x4B000000;
+}
+__device__ __forceinline__ int cell_index(double s, double cmax, double &fi) {
+    const double c = fmin(fmax(s, 0.0), cmax);
+    const double y = __dadd_rd(c, 4503599627370496.0);
+    fi = y - 4503599627370496.0;
+    return (int)(__double_as_longlong(y) - 0x4330000000000000ll);
+}
+
 // Cell along one axis: floor(Q / h) as one multiply by 1/h in the state
 // precision, clamped to [0, n-1]; frac = Q/h - i (the local coordinate).
 template <typename T>
-__device__ __forceinline__ int cell_of(T Q, T inv_h, int n, T &frac) {
+__device__ __forceinline__ int cell_of(T Q, T inv_h, T cmax, T &frac) {
     const T s = Q * inv_h;
-    const T f = flr(s);
-    const int i = (f >= T(0)) ? ((f < (T)n) ? (int)f : n - 1) : 0;     // NaN -> 0
-    frac = s - (T)i;
+    T fi;
+    const int i = cell_index(s, cmax, fi);
+    frac = s - fi;
     return i;
 }
 
@@ -86,6 +103,8 @@ __device__ double block_sum(double v, double *sh) {
     return s;
 }
 
+// v 2^k rounded to an integer; |v 2^k| < 2^62 or the flag is set.  FP32
+// values scale in FP32 (exact: a power of two) when 2^k is an FP32 normal.
 __device__ __forceinline__ unsigned long long to_fixed(double v, double scale, int *err) {
     const double x = v * scale;
     if (!(fabs(x) < 4.611686018427388e18)) {       // 2^62; also catches NaN
@@ -94,12 +113,23 @@ __device__ __forceinline__ unsigned long long to_fixed(double v, double scale, i
     }
     return (unsigned long long)__double2ll_rn(x);
 }
+__device__ __forceinline__ unsigned long long to_fixed(float v, double scale, int *err) {
+    if (scale < 0x1p-125 || scale > 0x1p125) return to_fixed((double)v, scale, err);
+    const float x = v * (float)scale;
+    if (!(fabsf(x) < 4.611686e18f)) {
+        atomicOr(err, isfinite(v) ? kErrOverflow : kErrNonFinite);
+        return 0ull;
+    }
+    return (unsigned long long)__float2ll_rn(x);
+}
 
 // ---------------------------------------------------------------------------
 // The fused particle pass
 // ---------------------------------------------------------------------------
+template <typename T> struct Part { T x, y, vx, vy, w, sx, sy, rx, ry; };
+
 template <typename T, bool DEC, bool DEP, bool DIAG>
-__global__ void __launch_bounds__(512) k_pass2d(PassArgs2d a) {
+__global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
     using T4 = typename V4<T>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[32];
@@ -121,17 +151,29 @@ __global__ void __launch_bounds__(512) k_pass2d(PassArgs2d a) {
     const T Lx = (T)a.Lx, Ly = (T)a.Ly, iLx = (T)a.inv_Lx, iLy = (T)a.inv_Ly;
     const T ihx = (T)a.inv_hx, ihy = (T)a.inv_hy;
     const T k1 = (T)a.k1, k2 = (T)a.k2, kd = (T)a.kd;
+    const T cmx = T(nx) - T(0.5), cmy = T(ny) - T(0.5);
     Kahan<T> s_m{T(0), T(0)}, s_x{T(0), T(0)}, s_y{T(0), T(0)}, s_k{T(0), T(0)};
 
+    // one particle per thread and turn; the next turn's particle is loaded
+    // before this one is pushed, so its loads are in flight meanwhile
+    auto load = [&](int64_t p, Part<T> &c) {
+        c.x = Qx[p]; c.y = Qy[p]; c.vx = Px[p]; c.vy = Py[p]; c.w = psi[p];
+        if (DEC) { c.sx = qx[p]; c.sy = qy[p]; c.rx = px[p]; c.ry = py[p]; }
+        else { c.sx = c.sy = c.rx = c.ry = T(0); }
+    };
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.n; p += stride) {
-        T x = Qx[p], y = Qy[p], vx = Px[p], vy = Py[p];
-        const T w = psi[p];
-        T sx = T(0), sy = T(0), rx = T(0), ry = T(0);     // q*, p*
-        if (DEC) { sx = qx[p]; sy = qy[p]; rx = px[p]; ry = py[p]; }
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    Part<T> cur;
+    if (p < a.n) load(p, cur);
+    for (; p < a.n; p += stride) {
+        Part<T> nxt;
+        if (p + stride < a.n) load(p + stride, nxt);
+        T x = cur.x, y = cur.y, vx = cur.vx, vy = cur.vy, sx = cur.sx, sy = cur.sy, rx = cur.rx, ry = cur.ry;
+        const T w = cur.w;
+        cur = nxt;
         // grad phi_h and H_ik = d_k g_i at Q from the four corners of the cell
         T xi, eta;
-        const int i = cell_of(x, ihx, nx, xi), j = cell_of(y, ihy, ny, eta);
+        const int i = cell_of(x, ihx, cmx, xi), j = cell_of(y, ihy, cmy, eta);
         const int i1 = (i + 1 == nx) ? 0 : i + 1, j1 = (j + 1 == ny) ? 0 : j + 1;
         const T4 c00 = tab[j * nx + i], c10 = tab[j * nx + i1], c01 = tab[j1 * nx + i], c11 = tab[j1 * nx + i1];
         const T oe = T(1) - eta, ox = T(1) - xi;
@@ -176,7 +218,7 @@ __global__ void __launch_bounds__(512) k_pass2d(PassArgs2d a) {
         if (DEP) {
             // psi* N_c(Q) - p* . grad N_c(Q) for the four corners
             T u, v;
-            const int di = cell_of(x, ihx, nx, u), dj = cell_of(y, ihy, ny, v);
+            const int di = cell_of(x, ihx, cmx, u), dj = cell_of(y, ihy, cmy, v);
             const int di1 = (di + 1 == nx) ? 0 : di + 1, dj1 = (dj + 1 == ny) ? 0 : dj + 1;
             const T ou = T(1) - u, ov = T(1) - v;
             const T ax = DEC ? rx * ihx : T(0), ay = DEC ? ry * ihy : T(0);
@@ -190,7 +232,7 @@ __global__ void __launch_bounds__(512) k_pass2d(PassArgs2d a) {
     if (DEP) {
         for (int k = threadIdx.x; k < nn; k += blockDim.x) {
             const T v = mesh[k];
-            if (v != T(0)) atomicAdd(a.acc + k, to_fixed((double)v, a.fx_scale, a.err));
+            if (v != T(0)) atomicAdd(a.acc + k, to_fixed(v, a.fx_scale, a.err));
         }
     }
     if (DIAG) {
