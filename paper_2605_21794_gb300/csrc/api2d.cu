@@ -32,9 +32,13 @@ struct swpic2d_ctx {
     double *b = nullptr, *phi = nullptr, *inv_lam = nullptr, *diag_acc = nullptr, *W = nullptr;
     double *rec = nullptr, *bsum = nullptr;
     double2 *spec = nullptr, *tw = nullptr;
+    float2 *twf = nullptr;
+    float *inv_lamf = nullptr;
+    unsigned int *done = nullptr;
     void *table = nullptr;
     int *err = nullptr;
     double fx_scale = 1.0, fx_inv = 1.0;
+    int fx_k = 0;
     int64_t step = 0, last_rec = -1, n_rec = 0, launches = 0;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;
     std::string msg;
@@ -59,7 +63,7 @@ int ilog2(int v) { int k = 0; while ((1 << k) < v) ++k; return k; }
 
 void free_all(swpic2d_ctx *c) {
     void *ptrs[] = {c->acc, c->b, c->phi, c->inv_lam, c->diag_acc, c->W, c->rec, c->bsum, c->spec, c->tw,
-                    c->table, c->err};
+                    c->table, c->err, c->twf, c->inv_lamf, c->done};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &e : c->events) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -96,7 +100,23 @@ SolveArgs2d solve_args(const swpic2d_ctx *c) {
     s.nx = c->cfg.nx; s.ny = c->cfg.ny;
     s.lognx = ilog2(c->cfg.nx); s.logny = ilog2(c->cfg.ny);
     s.ntw = std::max(c->cfg.nx, c->cfg.ny);
+    s.twf = c->twf;
+    s.inv_lamf = c->inv_lamf;
+    s.fx_k = c->fx_k;
     return s;
+}
+
+RecordArgs2d record_args(swpic2d_ctx *c, int64_t s) {
+    RecordArgs2d r{};
+    r.diag_acc = c->diag_acc;
+    r.W = c->W;
+    r.rec = (c->n_rec < c->cap) ? c->rec + 9 * c->n_rec : nullptr;   // full: later records dropped
+    r.err = c->err;
+    r.t = (double)s * c->cfg.dt;
+    r.area = c->cfg.Lx * c->cfg.Ly;
+    r.step = s;
+    if (c->n_rec < c->cap) ++c->n_rec;
+    return r;
 }
 
 swpic_status check_flag(swpic2d_ctx *ctx) {
@@ -110,12 +130,21 @@ swpic_status check_flag(swpic2d_ctx *ctx) {
     return SWPIC_OK;
 }
 
-// one fused pass: kick c1, diagnostics, kick c2, drift cd, deposit
-swpic_status pass(swpic2d_ctx *ctx, double c1, double c2, double cd, bool dep, bool diag) {
+// one fused pass: kick c1, diagnostics, kick c2, drift cd, deposit.  FP32:
+// the pass's last CTA also writes the record at integer step rec_step (diag)
+// and solves the new field (dep); FP64: separate record and solve kernels.
+swpic_status pass(swpic2d_ctx *ctx, double c1, double c2, double cd, bool dep, bool diag, int64_t rec_step) {
     PassArgs2d a = pass_args(ctx);
     a.k1 = c1 * ctx->cfg.dt;
     a.k2 = c2 * ctx->cfg.dt;
     a.kd = cd * ctx->cfg.dt;
+    const bool tail = ctx->prec == SWPIC_F32;
+    if (tail) {
+        a.tail = (diag ? 1 : 0) | (dep ? 2 : 0);
+        a.done = ctx->done;
+        if (diag) a.rec = record_args(ctx, rec_step);
+        a.solve = solve_args(ctx);
+    }
     const size_t smem = dep ? ctx->smem_dep : ctx->smem_nodep;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (ctx->timing) {
@@ -129,27 +158,13 @@ swpic_status pass(swpic2d_ctx *ctx, double c1, double c2, double cd, bool dep, b
         CK2(cudaEventRecord(e1, ctx->stream));
         ctx->events.emplace_back(e0, e1);
     }
-    return SWPIC_OK;
-}
-
-swpic_status solve(swpic2d_ctx *ctx) {
-    CK2(launch_solve(ctx->prec, solve_args(ctx), ctx->stream, &ctx->launches));
-    return SWPIC_OK;
-}
-
-swpic_status record(swpic2d_ctx *ctx, int64_t s) {
-    if (ctx->n_rec >= ctx->cap) return SWPIC_OK;         // full: later records dropped
-    RecordArgs2d r{};
-    r.diag_acc = ctx->diag_acc;
-    r.W = ctx->W;
-    r.rec = ctx->rec + 9 * ctx->n_rec;
-    r.err = ctx->err;
-    r.t = (double)s * ctx->cfg.dt;
-    r.area = ctx->cfg.Lx * ctx->cfg.Ly;
-    r.step = s;
-    CK2(launch_record(r, ctx->stream));
-    ++ctx->launches;
-    ++ctx->n_rec;
+    if (!tail) {
+        if (diag) {
+            CK2(launch_record(record_args(ctx, rec_step), ctx->stream));
+            ++ctx->launches;
+        }
+        if (dep) CK2(launch_solve(ctx->prec, solve_args(ctx), ctx->stream, &ctx->launches));
+    }
     return SWPIC_OK;
 }
 
@@ -200,6 +215,9 @@ swpic_status swpic2d_create(const swpic2d_config *cfg, int64_t n_particles, swpi
     alloc((void **)&ctx->bsum, sizeof(double));
     alloc((void **)&ctx->rec, sizeof(double) * 9 * ctx->cap);
     alloc((void **)&ctx->err, sizeof(int));
+    alloc((void **)&ctx->twf, sizeof(float2) * (ntw / 2));
+    alloc((void **)&ctx->inv_lamf, sizeof(float) * nn);
+    alloc((void **)&ctx->done, sizeof(unsigned int));
     if (!ok) {
         free_all(ctx);
         delete ctx;
@@ -220,7 +238,14 @@ swpic_status swpic2d_create(const swpic2d_config *cfg, int64_t n_particles, swpi
                                (2.0 - 2.0 * cy) * (4.0 + 2.0 * cx) * hx / (6.0 * hy);
             il[ky * c.nx + kx] = (kx == 0 && ky == 0) ? 0.0 : 1.0 / lam;
         }
+    std::vector<float2> twf(tw.size());
+    for (size_t k = 0; k < tw.size(); ++k) twf[k] = make_float2((float)tw[k].x, (float)tw[k].y);
+    std::vector<float> ilf(nn);
+    for (int k = 0; k < nn; ++k) ilf[k] = (float)il[k];
     bool okc = cudaMemcpy(ctx->tw, tw.data(), sizeof(double2) * tw.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemcpy(ctx->twf, twf.data(), sizeof(float2) * twf.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemcpy(ctx->inv_lamf, ilf.data(), sizeof(float) * nn, cudaMemcpyHostToDevice) == cudaSuccess &&
+               cudaMemset(ctx->done, 0, sizeof(unsigned int)) == cudaSuccess &&
                cudaMemcpy(ctx->inv_lam, il.data(), sizeof(double) * nn, cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemset(ctx->acc, 0, sizeof(unsigned long long) * nn) == cudaSuccess &&
                cudaMemset(ctx->table, 0, 4 * es * nn) == cudaSuccess &&
@@ -293,11 +318,10 @@ swpic_status swpic2d_refresh(swpic2d_ctx *ctx) {
     k = std::max(-1000, std::min(1000, k));
     ctx->fx_scale = std::ldexp(1.0, k);
     ctx->fx_inv = std::ldexp(1.0, -k);
+    ctx->fx_k = k;
     CK2(cudaMemsetAsync(ctx->acc, 0, sizeof(unsigned long long) * ctx->nn, ctx->stream));
     CK2(cudaMemsetAsync(ctx->diag_acc, 0, sizeof(double) * 4, ctx->stream));
-    swpic_status s = pass(ctx, 0.0, 0.0, 0.0, true, false);         // deposit only
-    if (s != SWPIC_OK) return s;
-    s = solve(ctx);
+    swpic_status s = pass(ctx, 0.0, 0.0, 0.0, true, false, 0);      // deposit, then the field
     if (s != SWPIC_OK) return s;
     CK2(cudaStreamSynchronize(ctx->stream));
     s = check_flag(ctx);
@@ -314,17 +338,9 @@ swpic_status swpic2d_step(swpic2d_ctx *ctx, int32_t n_steps, int32_t diag_every)
         const bool first = (p == 0), last = (p == n_steps);
         const int64_t s = ctx->step + p;           // integer time seen after the closing kick
         const bool diag = diag_every > 0 && s % diag_every == 0 && s != ctx->last_rec;
-        swpic_status st = pass(ctx, first ? 0.0 : 0.5, last ? 0.0 : 0.5, last ? 0.0 : 1.0, !last, diag);
+        swpic_status st = pass(ctx, first ? 0.0 : 0.5, last ? 0.0 : 0.5, last ? 0.0 : 1.0, !last, diag, s);
         if (st != SWPIC_OK) return st;
-        if (diag) {
-            st = record(ctx, s);
-            if (st != SWPIC_OK) return st;
-            ctx->last_rec = s;
-        }
-        if (!last) {
-            st = solve(ctx);
-            if (st != SWPIC_OK) return st;
-        }
+        if (diag) ctx->last_rec = s;
     }
     ctx->step += n_steps;
     return SWPIC_OK;

@@ -124,6 +124,155 @@ __device__ __forceinline__ unsigned long long to_fixed(float v, double scale, in
 }
 
 // ---------------------------------------------------------------------------
+// Diagnostic record and the one-CTA FP32 solve (the tail of an FP32 pass)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int bit_reverse(int i, int logn) {
+    return (logn == 0) ? 0 : (int)(__brev((unsigned)i) >> (32 - logn));
+}
+
+// One record from the pass's partial sums at the integer time and the field
+// energy of the field the pass used; clears the partial sums.  One thread.
+__device__ void write_record(const RecordArgs2d &r) {
+    if (r.rec) {
+        const double W = *r.W;
+        double *o = r.rec;
+        o[0] = r.t;
+        o[1] = r.diag_acc[0];
+        o[2] = r.diag_acc[1];
+        o[3] = r.diag_acc[2];
+        o[4] = r.diag_acc[3];
+        o[5] = W;
+        o[6] = r.diag_acc[3] + W;
+        o[7] = sqrt(fmax(2.0 * W / r.area, 0.0));
+        o[8] = (double)r.step;
+        if (!isfinite(o[6])) atomicOr(r.err, kErrNonFinite);
+    }
+    for (int q = 0; q < 4; ++q) r.diag_acc[q] = 0.0;
+}
+
+// Radix-2 DIT stages over the rows (stride 1, ROWS) or the columns (stride
+// nx) of an ny x nx complex FP32 array whose lines are in bit-reversed order.
+template <bool ROWS>
+__device__ void fft_lines_f32(float2 *z, int nx, int ny, const float2 *tw, int ntw, bool inverse) {
+    const int n = ROWS ? nx : ny, lines = ROWS ? ny : nx, half_n = n >> 1;
+    for (int len = 2; len <= n; len <<= 1) {
+        const int half = len >> 1, step = ntw / len;
+        for (int b = threadIdx.x; b < lines * half_n; b += blockDim.x) {
+            int line, r;
+            if (ROWS) { line = b / half_n; r = b - line * half_n; }
+            else { line = b % nx; r = b / nx; }
+            const int g = r / half, pos = r - g * half, k0 = g * len + pos;
+            const int i0 = ROWS ? line * nx + k0 : k0 * nx + line;
+            const int i1 = i0 + (ROWS ? half : half * nx);
+            float2 w = tw[pos * step];
+            if (inverse) w.y = -w.y;
+            const float2 u = z[i0], v = z[i1];
+            const float2 t = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
+            z[i0] = make_float2(u.x + t.x, u.y + t.y);
+            z[i1] = make_float2(u.x - t.x, u.y - t.y);
+        }
+        __syncthreads();
+    }
+}
+
+// In-place bit-reversal permutation of every row (ROWS) or column.
+template <bool ROWS>
+__device__ void brev_lines_f32(float2 *z, int nx, int ny, int logn) {
+    for (int b = threadIdx.x; b < nx * ny; b += blockDim.x) {
+        const int i = b % nx, j = b / nx;
+        const int k = ROWS ? i : j, r = bit_reverse(k, logn);
+        if (k < r) {
+            const int o = ROWS ? j * nx + r : r * nx + i;
+            const float2 t = z[b];
+            z[b] = z[o];
+            z[o] = t;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ long long block_sum_ll(long long v, long long *sh) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[w] = v;
+    __syncthreads();
+    long long s = 0;
+    for (int k = 0; k < nw; ++k) s += sh[k];
+    return s;                                   // every thread
+}
+
+// The new field from the accumulated node loads, by one CTA in FP32 (FP32
+// contexts): btilde = b - S/nn from the exact integers, forward DFT of the
+// rows and columns, division by the Q1 symbol (zero mode dropped), inverse
+// DFTs, W = (1/2) Phi^T btilde, the node table.  smem: 20 bytes per node.
+__device__ void solve_tail_f32(const SolveArgs2d &s, unsigned char *smem) {
+    __shared__ long long sh_ll[32];
+    __shared__ double sh_d[32];
+    const int nx = s.nx, ny = s.ny, nn = nx * ny, lognn = s.lognx + s.logny;
+    long long *bi = reinterpret_cast<long long *>(smem);
+    float2 *z = reinterpret_cast<float2 *>(smem + 8 * (size_t)nn);
+    float *bt = reinterpret_cast<float *>(smem + 16 * (size_t)nn);
+    long long part = 0;
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+        const long long v = (long long)__ldcg(s.acc + k);
+        s.acc[k] = 0ull;
+        bi[k] = v;
+        part += v;
+        s.b[k] = (double)v * s.fx_inv;
+    }
+    const long long S = block_sum_ll(part, sh_ll);
+    const long long q = S >> lognn, rem = S & (long long)(nn - 1);
+    const float frac = (float)rem * (float)s.inv_nn;
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+        const float v = scalbnf((float)(bi[k] - q) - frac, -s.fx_k);
+        bt[k] = v;
+        const int i = k % nx, j = k / nx;
+        z[j * nx + bit_reverse(i, s.lognx)] = make_float2(v, 0.0f);
+    }
+    __syncthreads();
+    fft_lines_f32<true>(z, nx, ny, s.twf, s.ntw, false);
+    brev_lines_f32<false>(z, nx, ny, s.logny);
+    fft_lines_f32<false>(z, nx, ny, s.twf, s.ntw, false);
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+        const float il = s.inv_lamf[k];
+        z[k] = make_float2(z[k].x * il, z[k].y * il);
+    }
+    __syncthreads();
+    brev_lines_f32<false>(z, nx, ny, s.logny);
+    fft_lines_f32<false>(z, nx, ny, s.twf, s.ntw, true);
+    brev_lines_f32<true>(z, nx, ny, s.lognx);
+    fft_lines_f32<true>(z, nx, ny, s.twf, s.ntw, true);
+    float *ph = reinterpret_cast<float *>(bi);            // the integers are no longer needed
+    const float inv_nn = (float)s.inv_nn;
+    double e = 0.0;
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+        const float phi = z[k].x * inv_nn;
+        ph[k] = phi;
+        s.phi[k] = (double)phi;
+        e += (double)(phi * bt[k]);
+    }
+    __syncthreads();
+    const float ihx = (float)s.inv_hx, ihy = (float)s.inv_hy;
+    for (int k = threadIdx.x; k < nn; k += blockDim.x) {
+        const int i = k % nx, j = k / nx;
+        const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
+        const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
+        auto cx = [&](int r) { return (ph[r * nx + ip] - ph[r * nx + im]) * (0.5f * ihx); };
+        auto cy = [&](int c) { return (ph[jp * nx + c] - ph[jm * nx + c]) * (0.5f * ihy); };
+        const float gx = (2.0f / 3.0f) * cx(j) + (1.0f / 6.0f) * (cx(jm) + cx(jp));
+        const float gy = (2.0f / 3.0f) * cy(i) + (1.0f / 6.0f) * (cy(im) + cy(ip));
+        reinterpret_cast<float4 *>(s.table)[k] = make_float4(ph[k], gx, gy, 0.0f);
+    }
+    const double Wt = block_sum(e, sh_d);
+    if (threadIdx.x == 0) {
+        *s.W = 0.5 * Wt;
+        if (!isfinite(Wt)) atomicOr(s.err, kErrNonFinite);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The fused particle pass
 // ---------------------------------------------------------------------------
 template <typename T> struct Part { T x, y, vx, vy, w, sx, sy, rx, ry; };
@@ -247,6 +396,21 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
             atomicAdd(a.diag_acc + 3, kk);
         }
     }
+    if constexpr (sizeof(T) == 4) {
+        if (!a.tail) return;
+        // the last CTA to finish (it sees every CTA's flush and partial sums)
+        // writes the record and solves the new field; no wait on other CTAs
+        __shared__ int s_last;
+        __threadfence();
+        __syncthreads();
+        if (threadIdx.x == 0) s_last = (atomicAdd(a.done, 1u) == gridDim.x - 1);
+        __syncthreads();
+        if (!s_last) return;
+        __threadfence();
+        if ((a.tail & 1) && threadIdx.x == 0) write_record(a.rec);
+        if (a.tail & 2) solve_tail_f32(a.solve, smem);
+        if (threadIdx.x == 0) *a.done = 0u;
+    }
 }
 
 // Bound of every partial sum of the deposit: sum psi* + 2 sum |p*_x|/hx +
@@ -269,10 +433,6 @@ __global__ void __launch_bounds__(256) k_bound2d(PassArgs2d a, double *out) {
 // ---------------------------------------------------------------------------
 // Spectral solve
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ int bit_reverse(int i, int logn) {
-    return (logn == 0) ? 0 : (int)(__brev((unsigned)i) >> (32 - logn));
-}
-
 // In-place radix-2 DFT of n = 2^logn points already in bit-reversed order
 // (sign -1 forward, +1 inverse; no normalisation).  All threads call it.
 __device__ void fft_inplace(double2 *z, int n, const double2 *tw, int ntw, bool inverse) {
@@ -374,20 +534,7 @@ __global__ void __launch_bounds__(256) k_table2d(SolveArgs2d s) {
 }
 
 __global__ void k_record2d(RecordArgs2d r) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    const double W = *r.W;
-    double *o = r.rec;
-    o[0] = r.t;
-    o[1] = r.diag_acc[0];
-    o[2] = r.diag_acc[1];
-    o[3] = r.diag_acc[2];
-    o[4] = r.diag_acc[3];
-    o[5] = W;
-    o[6] = r.diag_acc[3] + W;
-    o[7] = sqrt(fmax(2.0 * W / r.area, 0.0));
-    o[8] = (double)r.step;
-    if (!isfinite(o[6])) atomicOr(r.err, kErrNonFinite);
-    for (int q = 0; q < 4; ++q) r.diag_acc[q] = 0.0;
+    if (threadIdx.x == 0 && blockIdx.x == 0) write_record(r);
 }
 
 // ---------------------------------------------------------------------------

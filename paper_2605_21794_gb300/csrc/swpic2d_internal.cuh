@@ -11,6 +11,33 @@ namespace swpic2d {
 constexpr int kErrOverflow = 1;     // a CTA's node sum left the fixed-point range
 constexpr int kErrNonFinite = 2;    // non-finite charge or field energy
 
+// Arguments of the spectral solve and of the node table.
+struct SolveArgs2d {
+    unsigned long long *acc;      // in: node loads (cleared on read)
+    double *b;                    // out: node loads b (FP64)
+    double2 *spec;                // nx*ny complex work array, row-major (j nx + i)
+    double *phi;                  // out: zero-mean potential
+    const double *inv_lam;        // 1 / symbol per mode (0 for the zero mode)
+    const double2 *tw;            // exp(-2 pi i k / ntw), k < ntw/2
+    double *W;                    // out: (1/2) Phi^T b
+    void *table;                  // out: node table in the state precision
+    int *err;
+    double fx_inv, inv_hx, inv_hy, inv_nn;
+    int nx, ny, lognx, logny, ntw;
+    const float2 *twf;            // FP32 twiddles (the one-CTA FP32 solve)
+    const float *inv_lamf;        // FP32 inverse symbol
+    int fx_k;                     // fx_inv = 2^-fx_k
+};
+
+struct RecordArgs2d {
+    double *diag_acc;
+    const double *W;
+    double *rec;                  // 9 doubles per record
+    int *err;
+    double t, area;
+    int64_t step;
+};
+
 // Arguments of one fused particle pass: closing half-kick (c1 dt), the
 // diagnostics at the integer time, opening half-kick (c2 dt), drift (cd dt),
 // deposit of the drifted charge into the fixed-point accumulator.
@@ -26,30 +53,12 @@ struct PassArgs2d {
     double k1, k2, kd;            // c1 dt, c2 dt, cd dt
     double fx_scale;
     int nx, ny;
-};
-
-// Arguments of the spectral solve and of the node table.
-struct SolveArgs2d {
-    unsigned long long *acc;      // in: node loads (cleared on read)
-    double *b;                    // out: node loads b (FP64)
-    double2 *spec;                // nx*ny complex work array, row-major (j nx + i)
-    double *phi;                  // out: zero-mean potential
-    const double *inv_lam;        // 1 / symbol per mode (0 for the zero mode)
-    const double2 *tw;            // exp(-2 pi i k / ntw), k < ntw/2
-    double *W;                    // out: (1/2) Phi^T b
-    void *table;                  // out: node table in the state precision
-    int *err;
-    double fx_inv, inv_hx, inv_hy, inv_nn;
-    int nx, ny, lognx, logny, ntw;
-};
-
-struct RecordArgs2d {
-    double *diag_acc;
-    const double *W;
-    double *rec;                  // 9 doubles per record
-    int *err;
-    double t, area;
-    int64_t step;
+    // FP32 contexts: the last CTA to finish writes the diagnostic record
+    // (tail bit 0) and solves the new field in FP32 (tail bit 1)
+    int tail;
+    unsigned int *done;           // CTAs finished in this pass
+    RecordArgs2d rec;
+    SolveArgs2d solve;
 };
 
 size_t pass_smem_bytes(int prec, int nn, bool deposit);
