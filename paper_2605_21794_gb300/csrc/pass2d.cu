@@ -152,19 +152,21 @@ __device__ void write_record(const RecordArgs2d &r) {
 
 // Radix-2 DIT stages over the rows (stride 1, ROWS) or the columns (stride
 // nx) of an ny x nx complex FP32 array whose lines are in bit-reversed order.
+// nx = 2^lx, ny = 2^ly, ntw = 2^lt; tw in shared memory.
 template <bool ROWS>
-__device__ void fft_lines_f32(float2 *z, int nx, int ny, const float2 *tw, int ntw, bool inverse) {
-    const int n = ROWS ? nx : ny, lines = ROWS ? ny : nx, half_n = n >> 1;
-    for (int len = 2; len <= n; len <<= 1) {
-        const int half = len >> 1, step = ntw / len;
-        for (int b = threadIdx.x; b < lines * half_n; b += blockDim.x) {
+__device__ void fft_lines_f32(float2 *z, int lx, int ly, const float2 *tw, int lt, bool inverse) {
+    const int nx = 1 << lx;
+    const int ln = ROWS ? lx : ly, lh = ln - 1, total = 1 << (lx + ly - 1);
+    for (int s = 0; s < ln; ++s) {                  // half = 2^s, len = 2^(s+1)
+        const int half = 1 << s, tshift = lt - s - 1;
+        for (int b = threadIdx.x; b < total; b += blockDim.x) {
             int line, r;
-            if (ROWS) { line = b / half_n; r = b - line * half_n; }
-            else { line = b % nx; r = b / nx; }
-            const int g = r / half, pos = r - g * half, k0 = g * len + pos;
-            const int i0 = ROWS ? line * nx + k0 : k0 * nx + line;
-            const int i1 = i0 + (ROWS ? half : half * nx);
-            float2 w = tw[pos * step];
+            if (ROWS) { line = b >> lh; r = b & ((1 << lh) - 1); }
+            else { line = b & (nx - 1); r = b >> lx; }
+            const int g = r >> s, pos = r & (half - 1), k0 = (g << (s + 1)) + pos;
+            const int i0 = ROWS ? (line << lx) + k0 : (k0 << lx) + line;
+            const int i1 = i0 + (ROWS ? half : half << lx);
+            float2 w = tw[pos << tshift];
             if (inverse) w.y = -w.y;
             const float2 u = z[i0], v = z[i1];
             const float2 t = make_float2(v.x * w.x - v.y * w.y, v.x * w.y + v.y * w.x);
@@ -177,12 +179,13 @@ __device__ void fft_lines_f32(float2 *z, int nx, int ny, const float2 *tw, int n
 
 // In-place bit-reversal permutation of every row (ROWS) or column.
 template <bool ROWS>
-__device__ void brev_lines_f32(float2 *z, int nx, int ny, int logn) {
-    for (int b = threadIdx.x; b < nx * ny; b += blockDim.x) {
-        const int i = b % nx, j = b / nx;
-        const int k = ROWS ? i : j, r = bit_reverse(k, logn);
+__device__ void brev_lines_f32(float2 *z, int lx, int ly) {
+    const int nx = 1 << lx;
+    for (int b = threadIdx.x; b < (1 << (lx + ly)); b += blockDim.x) {
+        const int i = b & (nx - 1), j = b >> lx;
+        const int k = ROWS ? i : j, r = bit_reverse(k, ROWS ? lx : ly);
         if (k < r) {
-            const int o = ROWS ? j * nx + r : r * nx + i;
+            const int o = ROWS ? (j << lx) + r : (r << lx) + i;
             const float2 t = z[b];
             z[b] = z[o];
             z[o] = t;
@@ -225,26 +228,35 @@ __device__ void solve_tail_f32(const SolveArgs2d &s, unsigned char *smem) {
     const long long S = block_sum_ll(part, sh_ll);
     const long long q = S >> lognn, rem = S & (long long)(nn - 1);
     const float frac = (float)rem * (float)s.inv_nn;
+    const bool fsc = s.fx_k >= -125 && s.fx_k <= 125;       // 2^-k an FP32 normal: one exact multiply
+    const float sc = fsc ? (float)s.fx_inv : 1.0f;
+    const int lx = s.lognx, ly = s.logny;
+    int lt = 0;
+    while ((1 << lt) < s.ntw) ++lt;
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
-        const float v = scalbnf((float)(bi[k] - q) - frac, -s.fx_k);
+        const float u = (float)(bi[k] - q) - frac;
+        const float v = fsc ? u * sc : scalbnf(u, -s.fx_k);
         bt[k] = v;
-        const int i = k % nx, j = k / nx;
-        z[j * nx + bit_reverse(i, s.lognx)] = make_float2(v, 0.0f);
+        const int i = k & (nx - 1), j = k >> lx;
+        z[(j << lx) + bit_reverse(i, lx)] = make_float2(v, 0.0f);
     }
     __syncthreads();
-    fft_lines_f32<true>(z, nx, ny, s.twf, s.ntw, false);
-    brev_lines_f32<false>(z, nx, ny, s.logny);
-    fft_lines_f32<false>(z, nx, ny, s.twf, s.ntw, false);
+    float2 *tw = reinterpret_cast<float2 *>(bi);             // the integers are no longer needed
+    for (int k = threadIdx.x; k < (s.ntw >> 1); k += blockDim.x) tw[k] = s.twf[k];
+    __syncthreads();
+    fft_lines_f32<true>(z, lx, ly, tw, lt, false);
+    brev_lines_f32<false>(z, lx, ly);
+    fft_lines_f32<false>(z, lx, ly, tw, lt, false);
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
         const float il = s.inv_lamf[k];
         z[k] = make_float2(z[k].x * il, z[k].y * il);
     }
     __syncthreads();
-    brev_lines_f32<false>(z, nx, ny, s.logny);
-    fft_lines_f32<false>(z, nx, ny, s.twf, s.ntw, true);
-    brev_lines_f32<true>(z, nx, ny, s.lognx);
-    fft_lines_f32<true>(z, nx, ny, s.twf, s.ntw, true);
-    float *ph = reinterpret_cast<float *>(bi);            // the integers are no longer needed
+    brev_lines_f32<false>(z, lx, ly);
+    fft_lines_f32<false>(z, lx, ly, tw, lt, true);
+    brev_lines_f32<true>(z, lx, ly);
+    fft_lines_f32<true>(z, lx, ly, tw, lt, true);
+    float *ph = reinterpret_cast<float *>(bi);            // the twiddles are no longer needed
     const float inv_nn = (float)s.inv_nn;
     double e = 0.0;
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
@@ -256,11 +268,11 @@ __device__ void solve_tail_f32(const SolveArgs2d &s, unsigned char *smem) {
     __syncthreads();
     const float ihx = (float)s.inv_hx, ihy = (float)s.inv_hy;
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
-        const int i = k % nx, j = k / nx;
-        const int im = (i == 0) ? nx - 1 : i - 1, ip = (i == nx - 1) ? 0 : i + 1;
-        const int jm = (j == 0) ? ny - 1 : j - 1, jp = (j == ny - 1) ? 0 : j + 1;
-        auto cx = [&](int r) { return (ph[r * nx + ip] - ph[r * nx + im]) * (0.5f * ihx); };
-        auto cy = [&](int c) { return (ph[jp * nx + c] - ph[jm * nx + c]) * (0.5f * ihy); };
+        const int i = k & (nx - 1), j = k >> lx;
+        const int im = (i - 1) & (nx - 1), ip = (i + 1) & (nx - 1);
+        const int jm = (j - 1) & (ny - 1), jp = (j + 1) & (ny - 1);
+        auto cx = [&](int r) { return (ph[(r << lx) + ip] - ph[(r << lx) + im]) * (0.5f * ihx); };
+        auto cy = [&](int c) { return (ph[(jp << lx) + c] - ph[(jm << lx) + c]) * (0.5f * ihy); };
         const float gx = (2.0f / 3.0f) * cx(j) + (1.0f / 6.0f) * (cx(jm) + cx(jp));
         const float gy = (2.0f / 3.0f) * cy(i) + (1.0f / 6.0f) * (cy(im) + cy(ip));
         reinterpret_cast<float4 *>(s.table)[k] = make_float4(ph[k], gx, gy, 0.0f);
