@@ -98,8 +98,9 @@ swpic_status swpic2d_diagnostics(swpic2d_ctx *ctx, swpic2d_diag *out, int32_t ma
 
 /* Synchronous: the current field on the nodes, host arrays of ny*nx doubles
  * (node index j nx + i); any pointer may be NULL.  b is the deposited load
- * of the last field update, Phi the zero-mean potential, gx, gy the projected
- * gradient held (rounded to the state precision) in the node table. */
+ * of the last field update, Phi the zero-mean potential (FP32 contexts: the
+ * FP32 values of the node table), gx, gy the projected gradient held
+ * (rounded to the state precision) in the node table. */
 swpic_status swpic2d_get_field(swpic2d_ctx *ctx, double *b, double *Phi, double *gx, double *gy);
 
 /* Synchronous: wait for the stream; report a device anomaly flag. */

@@ -35,6 +35,7 @@ struct swpic2d_ctx {
     float2 *twf = nullptr;
     float *inv_lamf = nullptr;
     unsigned int *done = nullptr;
+    long long *braw = nullptr;
     void *table = nullptr;
     int *err = nullptr;
     double fx_scale = 1.0, fx_inv = 1.0;
@@ -63,7 +64,7 @@ int ilog2(int v) { int k = 0; while ((1 << k) < v) ++k; return k; }
 
 void free_all(swpic2d_ctx *c) {
     void *ptrs[] = {c->acc, c->b, c->phi, c->inv_lam, c->diag_acc, c->W, c->rec, c->bsum, c->spec, c->tw,
-                    c->table, c->err, c->twf, c->inv_lamf, c->done};
+                    c->table, c->err, c->twf, c->inv_lamf, c->done, c->braw};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     for (auto &e : c->events) { cudaEventDestroy(e.first); cudaEventDestroy(e.second); }
@@ -103,6 +104,7 @@ SolveArgs2d solve_args(const swpic2d_ctx *c) {
     s.twf = c->twf;
     s.inv_lamf = c->inv_lamf;
     s.fx_k = c->fx_k;
+    s.braw = c->braw;
     return s;
 }
 
@@ -218,6 +220,7 @@ swpic_status swpic2d_create(const swpic2d_config *cfg, int64_t n_particles, swpi
     alloc((void **)&ctx->twf, sizeof(float2) * (ntw / 2));
     alloc((void **)&ctx->inv_lamf, sizeof(float) * nn);
     alloc((void **)&ctx->done, sizeof(unsigned int));
+    alloc((void **)&ctx->braw, sizeof(long long) * nn);
     if (!ok) {
         free_all(ctx);
         delete ctx;
@@ -246,6 +249,7 @@ swpic_status swpic2d_create(const swpic2d_config *cfg, int64_t n_particles, swpi
                cudaMemcpy(ctx->twf, twf.data(), sizeof(float2) * twf.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemcpy(ctx->inv_lamf, ilf.data(), sizeof(float) * nn, cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemset(ctx->done, 0, sizeof(unsigned int)) == cudaSuccess &&
+               cudaMemset(ctx->braw, 0, sizeof(long long) * nn) == cudaSuccess &&
                cudaMemcpy(ctx->inv_lam, il.data(), sizeof(double) * nn, cudaMemcpyHostToDevice) == cudaSuccess &&
                cudaMemset(ctx->acc, 0, sizeof(unsigned long long) * nn) == cudaSuccess &&
                cudaMemset(ctx->table, 0, 4 * es * nn) == cudaSuccess &&
@@ -366,21 +370,31 @@ swpic_status swpic2d_get_field(swpic2d_ctx *ctx, double *b, double *Phi, double 
     if (!ctx) return SWPIC_EINVAL;
     CK2(cudaStreamSynchronize(ctx->stream));
     const int nn = ctx->nn;
-    if (b) CK2(cudaMemcpy(b, ctx->b, sizeof(double) * nn, cudaMemcpyDeviceToHost));
-    if (Phi) CK2(cudaMemcpy(Phi, ctx->phi, sizeof(double) * nn, cudaMemcpyDeviceToHost));
-    if (gx || gy) {
+    const bool f32 = ctx->prec == SWPIC_F32;       // FP32: integer loads and the FP32 Phi of the table
+    if (b && f32) {
+        std::vector<long long> raw(nn);
+        CK2(cudaMemcpy(raw.data(), ctx->braw, sizeof(long long) * nn, cudaMemcpyDeviceToHost));
+        for (int k = 0; k < nn; ++k) b[k] = (double)raw[k] * ctx->fx_inv;
+    } else if (b) {
+        CK2(cudaMemcpy(b, ctx->b, sizeof(double) * nn, cudaMemcpyDeviceToHost));
+    }
+    if (Phi && !f32) CK2(cudaMemcpy(Phi, ctx->phi, sizeof(double) * nn, cudaMemcpyDeviceToHost));
+    if (gx || gy || (Phi && f32)) {
         const size_t es = (ctx->prec == SWPIC_F64) ? 8 : 4;
         std::vector<unsigned char> t(4 * es * nn);
         CK2(cudaMemcpy(t.data(), ctx->table, t.size(), cudaMemcpyDeviceToHost));
         for (int k = 0; k < nn; ++k) {
-            double vx, vy;
+            double vp, vx, vy;
             if (es == 8) {
+                vp = reinterpret_cast<const double *>(t.data())[4 * k];
                 vx = reinterpret_cast<const double *>(t.data())[4 * k + 1];
                 vy = reinterpret_cast<const double *>(t.data())[4 * k + 2];
             } else {
+                vp = reinterpret_cast<const float *>(t.data())[4 * k];
                 vx = reinterpret_cast<const float *>(t.data())[4 * k + 1];
                 vy = reinterpret_cast<const float *>(t.data())[4 * k + 2];
             }
+            if (Phi && f32) Phi[k] = vp;
             if (gx) gx[k] = vx;
             if (gy) gy[k] = vy;
         }

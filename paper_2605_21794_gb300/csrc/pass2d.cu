@@ -223,7 +223,7 @@ __device__ void solve_tail_f32(const SolveArgs2d &s, unsigned char *smem) {
         s.acc[k] = 0ull;
         bi[k] = v;
         part += v;
-        s.b[k] = (double)v * s.fx_inv;
+        s.braw[k] = v;                  // the read-out scales it on the host
     }
     const long long S = block_sum_ll(part, sh_ll);
     const long long q = S >> lognn, rem = S & (long long)(nn - 1);
@@ -258,12 +258,11 @@ __device__ void solve_tail_f32(const SolveArgs2d &s, unsigned char *smem) {
     fft_lines_f32<true>(z, lx, ly, tw, lt, true);
     float *ph = reinterpret_cast<float *>(bi);            // the twiddles are no longer needed
     const float inv_nn = (float)s.inv_nn;
-    double e = 0.0;
+    float e = 0.0f;
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
         const float phi = z[k].x * inv_nn;
-        ph[k] = phi;
-        s.phi[k] = (double)phi;
-        e += (double)(phi * bt[k]);
+        ph[k] = phi;                    // Phi is read out from the node table
+        e += phi * bt[k];
     }
     __syncthreads();
     const float ihx = (float)s.inv_hx, ihy = (float)s.inv_hy;
@@ -277,7 +276,7 @@ __device__ void solve_tail_f32(const SolveArgs2d &s, unsigned char *smem) {
         const float gy = (2.0f / 3.0f) * cy(i) + (1.0f / 6.0f) * (cy(im) + cy(ip));
         reinterpret_cast<float4 *>(s.table)[k] = make_float4(ph[k], gx, gy, 0.0f);
     }
-    const double Wt = block_sum(e, sh_d);
+    const double Wt = block_sum((double)e, sh_d);
     if (threadIdx.x == 0) {
         *s.W = 0.5 * Wt;
         if (!isfinite(Wt)) atomicOr(s.err, kErrNonFinite);

@@ -27,6 +27,7 @@ struct SolveArgs2d {
     const float2 *twf;            // FP32 twiddles (the one-CTA FP32 solve)
     const float *inv_lamf;        // FP32 inverse symbol
     int fx_k;                     // fx_inv = 2^-fx_k
+    long long *braw;              // FP32 solve: the integer node loads of the last update
 };
 
 struct RecordArgs2d {
