@@ -379,11 +379,11 @@ def profiled_traffic(name="k_pass_bump_on_tail_4096"):
     """DRAM bytes per launch of the fused pass from the committed ncu summary,
     valid only while the kernel source is the one that was profiled."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2605_21794_gb300", "csrc", "pass.cu")
     summ = os.path.join(ROOT, "profiles", name + ".json")
     try:
         with open(summ) as f:
             d = json.load(f)
+        src = os.path.join(ROOT, "paper_2605_21794_gb300", "csrc", d.get("source", "pass.cu"))
         h = hashlib.sha256(open(src, "rb").read()).hexdigest()
         if d.get("pass_cu_sha256") == h:
             return d.get("dram_bytes_per_launch_full_size")
@@ -563,7 +563,8 @@ def two_d_leg(torch, swpic, args):
             "value": n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "avg_launch_ms": avg,
+                         "frac": achieved / peak, "avg_launch_ms": avg,
+                         "traffic": profiled_traffic("k_pass2d_landau2d_4096x4096") if n == 1 << 24 else None,
                          "kernel": "k_pass2d<float, decorated, deposit, diag>",
                          "algorithmic_bytes_per_launch": bpp * n, "peak_source": peak_src},
             "max_abs_dH_over_H0": float(np.max(np.abs(H - H[0])) / abs(H[0])),
