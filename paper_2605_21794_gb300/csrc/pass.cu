@@ -834,42 +834,47 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
     const int64_t step = (int64_t)U * blockDim.x;                // vectors per CTA iteration
     // warp w takes the N = TurnVecs<T>::n consecutive vectors v0 + k step + N w + [0, N)
     // in its k-th turn, lane l the vectors l, 32 + l, ... of them; the trip count is
-    // warp-uniform and out-of-range lanes carry empty deposit slots
-    for (int64_t vb = v0 + (int64_t)U * (threadIdx.x - lane); vb < v1; vb += step) {
-        V q[U], p[U], x[U], y[U], m[U];
-        bool ok[U];
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            const int64_t vv = vb + 32 * u + lane;
-            ok[u] = vv < v1;
-            if (ok[u]) {
-                q[u] = reinterpret_cast<const V *>(Qi)[vv];
-                p[u] = reinterpret_cast<const V *>(Pi)[vv];
-                m[u] = reinterpret_cast<const V *>(wi)[vv];
-                if (DEC) {
-                    x[u] = reinterpret_cast<const V *>(qsi)[vv];
-                    y[u] = reinterpret_cast<const V *>(psi)[vv];
-                }
-            }
+    // warp-uniform and out-of-range lanes carry empty deposit slots.  A thread walks
+    // its vectors in that order one at a time, and loads the next one before it
+    // pushes the current one, so a vector's loads are always in flight.
+    const int64_t vb0 = v0 + (int64_t)U * (threadIdx.x - lane);
+    const int64_t nturn = (vb0 < v1) ? (v1 - vb0 + step - 1) / step : 0;
+    const int64_t total = nturn * U;
+    struct Vin { V q, p, x, y, m; };
+    auto vec_of = [&](int64_t t) { return vb0 + (t / U) * step + 32 * (t % U) + lane; };
+    auto load = [&](int64_t vv, Vin &c) {
+        c.q = reinterpret_cast<const V *>(Qi)[vv];
+        c.p = reinterpret_cast<const V *>(Pi)[vv];
+        c.m = reinterpret_cast<const V *>(wi)[vv];
+        if (DEC) {
+            c.x = reinterpret_cast<const V *>(qsi)[vv];
+            c.y = reinterpret_cast<const V *>(psi)[vv];
         }
-#pragma unroll
-        for (int u = 0; u < U; ++u) {
-            VecOut<T> o;
-            if (ok[u]) {
-                push_vector<T, DEC, DEP, DIAG, D2>(q[u], p[u], x[u], y[u], m[u], s_tab, nx, G, k1, k2, kd, th, o);
-                const int64_t vv = vb + 32 * u + lane;
-                reinterpret_cast<V *>(Qo)[vv] = q[u];
-                reinterpret_cast<V *>(Po)[vv] = p[u];
-                if (DEC) {
-                    reinterpret_cast<V *>(qso)[vv] = x[u];
-                    reinterpret_cast<V *>(pso)[vv] = y[u];
-                }
-                if (wpsi) reinterpret_cast<V *>(wo)[vv] = m[u];
-            } else {
-                o.clear();
+    };
+    Vin cur;
+    bool cur_ok = total > 0 && vec_of(0) < v1;
+    if (cur_ok) load(vec_of(0), cur);
+    for (int64_t t = 0; t < total; ++t) {
+        Vin nxt;
+        const bool nxt_ok = t + 1 < total && vec_of(t + 1) < v1;
+        if (nxt_ok) load(vec_of(t + 1), nxt);
+        VecOut<T> o;
+        if (cur_ok) {
+            push_vector<T, DEC, DEP, DIAG, D2>(cur.q, cur.p, cur.x, cur.y, cur.m, s_tab, nx, G, k1, k2, kd, th, o);
+            const int64_t vv = vec_of(t);
+            reinterpret_cast<V *>(Qo)[vv] = cur.q;
+            reinterpret_cast<V *>(Po)[vv] = cur.p;
+            if (DEC) {
+                reinterpret_cast<V *>(qso)[vv] = cur.x;
+                reinterpret_cast<V *>(pso)[vv] = cur.y;
             }
-            if (DEP) deposit_vector<T, MODE, D2 == SWPIC_D2_P2>(o, s_mesh, s_mesh_m, scale, err);
+            if (wpsi) reinterpret_cast<V *>(wo)[vv] = cur.m;
+        } else {
+            o.clear();
         }
+        if (DEP) deposit_vector<T, MODE, D2 == SWPIC_D2_P2>(o, s_mesh, s_mesh_m, scale, err);
+        cur = nxt;
+        cur_ok = nxt_ok;
     }
     for (int64_t k = ve + threadIdx.x; k < e; k += blockDim.x) scalar(k);
 }
