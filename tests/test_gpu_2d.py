@@ -181,3 +181,30 @@ def test_workload_size_properties():
     assert f1["b"].sum() == pytest.approx(total, rel=1e-6)
     assert np.all(np.isfinite(d)) and d.shape[0] == 6
     np.testing.assert_allclose(d[:, 1], total, rtol=1e-6)
+
+
+@pytest.mark.parametrize("nx,ny", [(4, 256), (256, 4)])
+def test_extreme_aspect_meshes_fp64(nx, ny):
+    """The smallest axis (4 cells) against the longest (256): one FP64 step."""
+    need_gpu()
+    Lx, Ly, dt = 2.0 * nx / 16, 2.0 * ny / 16, 0.05
+    st = W.random_state_2d(3000, Lx, Ly, seed=16, nx=nx, ny=ny, alpha=0.2)
+    got, diag, _ = _run(64, st, Lx, Ly, nx, ny, dt, 2, diag_every=1)
+    ref = O.run2d(st, nx, ny, Lx, Ly, dt, 2, diag_every=1)
+    _compare(got, ref, Lx, Ly, 1e-11)
+    for c in range(1, 8):
+        assert rel_max(diag[:, c], ref["diag"][:, c]) < 1e-10, c
+
+
+def test_fp32_point_particles_and_largest_fp32_mesh():
+    """Undecorated FP32 particles on the largest FP32 mesh (128 x 64 = 8192
+    nodes: the table and mesh fill 160 KB of shared memory) against the
+    FP32-storage oracle, whose dense solve is the slow part here."""
+    need_gpu()
+    Lx, Ly, nx, ny, dt = 8.0, 4.0, 128, 64, 0.05
+    st = _cast(W.random_state_2d(30000, Lx, Ly, seed=17, nx=nx, ny=ny, decorated=False, alpha=0.3), 32)
+    got, diag, _ = _run(32, st, Lx, Ly, nx, ny, dt, 1, decorated=False)
+    ref = O.run2d(st, nx, ny, Lx, Ly, dt, 1, diag_every=1, decorated=False, store_f32=True)
+    _compare(got, ref, Lx, Ly, 1e-5, KEYS[:4])
+    for c in (1, 2, 3, 4, 5, 7):
+        assert rel_max(diag[:, c], ref["diag"][:, c]) < 1e-4, c
