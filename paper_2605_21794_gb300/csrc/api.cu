@@ -324,7 +324,9 @@ swpic_status prepare(swpic_ctx *ctx, bool keep_steps) {
     if (s != SWPIC_OK) return s;
     ctx->last_diag_step = ctx->step;
     ctx->prepared = true;
-    clear_graphs(ctx);
+    // the captured step graphs stay valid: they hold the bound pointers and the
+    // launch shape (both clear them when they change), and read the unit, the
+    // step counters and the field from device memory
     return SWPIC_OK;
 }
 
