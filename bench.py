@@ -256,7 +256,7 @@ def main():
 
     sim = make(mode, args.resort)
     # every leg starts from the initial state: the decorations of this workload
-    # grow without bound late in the run (see DESIGN.md), so no leg runs past
+    # grow without bound late in the run, so no leg runs past
     # warm-up + K steps from t = 0
     torch.cuda.synchronize()
     init_state = [t.clone() for t in (sim.Q, sim.P, sim.qs, sim.ps, sim.psi)]

@@ -1,4 +1,4 @@
-"""Closed-form physics used to pin the oracle and to judge long runs.
+"""Closed-form physics used to pin the oracle and to assess long runs.
 
 * Kinetic dispersion relations of the 1D Vlasov-Poisson system (e = m =
   eps0 = 1) in terms of the plasma dispersion function Z, evaluated with
