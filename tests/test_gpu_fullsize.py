@@ -135,3 +135,29 @@ def test_ensemble_full_size_one_batched_step():
         sl = slice(off[i], off[i + 1])
         g = {k: v[sl] for k, v in got.items()}
         _check_sample(g, ref, np.arange(lat.n), lat.L, 1e-6)
+
+
+def test_bump_on_tail_full_size_one_fp32_step_p2_field():
+    """The benchmark workload with the P2 field (its own bench leg): 16.7M
+    decorated FP32 particles, nx 1024, in the launch shape that leg tunes to
+    (256 x 3, bulk copy), one step against the oracle's dense P2 solve."""
+    need_gpu()
+    from paper_2605_21794_gb300 import swpic
+    spec = W.bump_on_tail()
+    lat = spec.lattice
+    sim = _sim([(lat.L, spec.dt, spec.nx, lat.n)], 32, d2_mode=swpic.SWPIC_D2_P2, threads_per_block=256,
+               blocks_per_sm=3, pipeline_stages=3)
+    try:
+        sim.init_lattice(0, lat)
+        sim.step(1, diag_every=1)
+        got = sim.state()
+        d = sim.diagnostics()
+    finally:
+        sim.close()
+    st = cast_state(O.init_lattice(lat), 32)
+    ref = O.run(st, spec.nx, lat.L, spec.dt, 1, diag_every=1, d2_mode=swpic.SWPIC_D2_P2, store_f32=True)
+    rng = np.random.default_rng(6)
+    idx = np.sort(rng.choice(lat.n, SAMPLE, replace=False))
+    _check_sample(got, ref, idx, lat.L, 1e-6)
+    for col in (4, 6):            # P2 field energy and E_amp, both records
+        assert rel_max(d[:, col], ref["diag"][:, col]) < 1e-5, col
