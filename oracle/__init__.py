@@ -100,6 +100,8 @@ def lib():
                                   C.c_int32, _D, _D, _D, _D, _D, _D, _D, _D, _D]
         L.or2d_field_energy.restype = C.c_double
         L.or2d_field_energy.argtypes = [C.c_int32, C.c_int32, C.c_double, C.c_double, _D]
+        L.or2d_init_lattice.restype = C.c_int
+        L.or2d_init_lattice.argtypes = [C.c_int32] * 4 + [C.c_double] * 8 + [C.c_int32, C.c_int32] + [_D] * 9
         L.or2d_run.restype = C.c_int
         L.or2d_run.argtypes = [C.c_int64, _D, _D, _D, _D, _D, _D, _D, _D, _D, C.c_int32, C.c_int32,
                                C.c_double, C.c_double, C.c_double, C.c_int32, C.c_int32, C.c_int32,
@@ -483,4 +485,18 @@ def run2d(state, nx, ny, Lx, Ly, dt, n_steps, diag_every=1, decorated=True, stor
         raise RuntimeError("2D oracle run failed")
     st["diag"] = diag[: nd.value]
     st["Phi"] = Phi
+    return st
+
+
+def init_lattice2d(spec):
+    """2D2V lattice state of a workloads.Lattice2DSpec (cluster reading of
+    Sec. 4.2 in 2D2V; see or2d_init_lattice)."""
+    n = spec.n
+    st = {k: np.zeros(n) for k in STATE2D}
+    rc = lib().or2d_init_lattice(int(spec.nqx), int(spec.nqy), int(spec.nvx), int(spec.nvy), float(spec.Lx),
+                                 float(spec.Ly), float(spec.vmin), float(spec.vmax), float(spec.alpha),
+                                 float(spec.kx), float(spec.ky), float(spec.vth), int(spec.quad_order),
+                                 int(bool(spec.decorate)), *[_d(st[k]) for k in STATE2D])
+    if rc != 0:
+        raise ValueError("bad 2D lattice")
     return st

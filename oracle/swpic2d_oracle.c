@@ -437,3 +437,63 @@ int or2d_run(int64_t n, double *Qx, double *Qy, double *Px, double *Py, double *
     for (int k = 0; k < 6; ++k) free(*pa[k]);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Lattice initialisation in 2D2V: the reading of Sec. 4.2 / Alg. 1 used in   */
+/* 1D, one dimension up.  Each cell of a 4D phase-space lattice is the        */
+/* cluster S_a of the continuum f0; particle index ((i nqy + j) nvx + k) nvy  */
+/* + l;  Q = cell centre in (x, y), P = cell centre in (vx, vy);              */
+/*   psi*  = f0(centre) dx dy dvx dvy                        (midpoint)        */
+/*   p*_x  = int_cell f0 (Lx/2pi) sin(2pi (Qx - x)/Lx)   (periodic c, Sec. 4.2) */
+/*   p*_y  = int_cell f0 (Ly/2pi) sin(2pi (Qy - y)/Ly)                         */
+/*   q*    = - int_cell f0 (P - p)                          (Eq. moment-def)  */
+/* by an n^4 Gauss-Legendre rule.                                             */
+/* f0 = (1 + alpha cos(kx x + ky y)) exp(-(vx^2 + vy^2)/(2 vth^2)) / (2 pi vth^2) */
+/* ------------------------------------------------------------------------ */
+int or_gauss_legendre(int32_t npts, double *x, double *w);
+
+static double f0_2d(double alpha, double kx, double ky, double vth, double x, double y, double vx, double vy) {
+    const double pi = 3.14159265358979323846;
+    return (1.0 + alpha * cos(kx * x + ky * y)) * exp(-(vx * vx + vy * vy) / (2.0 * vth * vth)) /
+           (2.0 * pi * vth * vth);
+}
+
+int or2d_init_lattice(int32_t nqx, int32_t nqy, int32_t nvx, int32_t nvy, double Lx, double Ly,
+                      double vmin, double vmax, double alpha, double kx, double ky, double vth,
+                      int32_t quad_order, int32_t decorate, double *Qx, double *Qy, double *Px, double *Py,
+                      double *qx, double *qy, double *px, double *py, double *psi) {
+    if (nqx < 1 || nqy < 1 || nvx < 1 || nvy < 1 || quad_order < 1 || quad_order > 8) return -1;
+    double g[64], gw[64];
+    if (or_gauss_legendre(quad_order, g, gw) != 0) return -1;
+    const double pi = 3.14159265358979323846;
+    const double dx = Lx / nqx, dy = Ly / nqy, dvx = (vmax - vmin) / nvx, dvy = (vmax - vmin) / nvy;
+    const int32_t n = quad_order;
+    for (int32_t i = 0; i < nqx; ++i)
+        for (int32_t j = 0; j < nqy; ++j)
+            for (int32_t k = 0; k < nvx; ++k)
+                for (int32_t l = 0; l < nvy; ++l) {
+                    const int64_t a = (((int64_t)i * nqy + j) * nvx + k) * nvy + l;
+                    const double xc = (i + 0.5) * dx, yc = (j + 0.5) * dy;
+                    const double uc = vmin + (k + 0.5) * dvx, wc = vmin + (l + 0.5) * dvy;
+                    Qx[a] = xc; Qy[a] = yc; Px[a] = uc; Py[a] = wc;
+                    psi[a] = f0_2d(alpha, kx, ky, vth, xc, yc, uc, wc) * dx * dy * dvx * dvy;
+                    double sx = 0.0, sy = 0.0, tx = 0.0, ty = 0.0;
+                    if (decorate) {
+                        for (int32_t r = 0; r < n; ++r)
+                            for (int32_t s = 0; s < n; ++s)
+                                for (int32_t t = 0; t < n; ++t)
+                                    for (int32_t u = 0; u < n; ++u) {
+                                        const double x = xc + 0.5 * dx * g[r], y = yc + 0.5 * dy * g[s];
+                                        const double vx = uc + 0.5 * dvx * g[t], vy = wc + 0.5 * dvy * g[u];
+                                        const double wgt = gw[r] * gw[s] * gw[t] * gw[u] * 0.0625 * dx * dy * dvx * dvy;
+                                        const double fv = wgt * f0_2d(alpha, kx, ky, vth, x, y, vx, vy);
+                                        sx += fv * (Lx / (2.0 * pi)) * sin(2.0 * pi * (xc - x) / Lx);
+                                        sy += fv * (Ly / (2.0 * pi)) * sin(2.0 * pi * (yc - y) / Ly);
+                                        tx += -fv * (uc - vx);
+                                        ty += -fv * (wc - vy);
+                                    }
+                    }
+                    px[a] = sx; py[a] = sy; qx[a] = tx; qy[a] = ty;
+                }
+    return 0;
+}

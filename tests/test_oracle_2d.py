@@ -212,3 +212,43 @@ def test_fp32_cell_decision():
     q = Q.astype(np.float32)
     ref = np.clip(np.floor(q * np.float32(n / L)), 0, n - 1).astype(np.int32)
     np.testing.assert_array_equal(got, ref)
+
+
+def test_lattice_init_with_ky_zero_factors_into_the_1d_init():
+    """ky = 0: f0 = (1 + alpha cos kx x) M(vx) M(vy), so every 2D decoration
+    is the pinned 1D one (same x-vx lattice, Maxwellian term) times the
+    y-vy cell integral of M(vy) by the same Gauss rule; p*_y vanishes (odd
+    integrand over a centred cell) and q*_y is the vy cell moment."""
+    nq, nv, n, L, Ly = 8, 12, 3, 4 * np.pi, 3.0
+    sp2 = W.Lattice2DSpec(nq, 2, nv, 6, L, Ly, -6.0, 6.0, 0.3, 0.5, 0.0, 1.0, n, True)
+    st2 = O.init_lattice2d(sp2)
+    lat1 = W.LatticeSpec(nq, nv, L, -6.0, 6.0, 0.3, 0.5, W.MAXWELL, quad_order=n)
+    st1 = O.init_lattice(lat1)
+    g, gw = O.gauss_legendre(n)
+    dy, dvy = Ly / 2, 12.0 / 6
+    M = lambda v: np.exp(-v * v / 2) / np.sqrt(2 * np.pi)
+    a = np.arange(sp2.n)
+    i, j, k, l = a // (2 * nv * 6), (a // (nv * 6)) % 2, (a // 6) % nv, a % 6
+    one = i * nv + k                                        # the 1D particle of (i, k)
+    wc = -6.0 + (l + 0.5) * dvy
+    vy = wc[:, None] + 0.5 * dvy * g[None, :]
+    Imy = (gw[None, :] * 0.5 * dvy * M(vy)).sum(1) * dy          # int_cell dy dvy M(vy)
+    Imy1 = (gw[None, :] * 0.5 * dvy * M(vy) * (wc[:, None] - vy)).sum(1) * dy
+    np.testing.assert_allclose(st2["psi"], st1["psi"][one] * M(wc) * dy * dvy, rtol=1e-13)
+    np.testing.assert_allclose(st2["px"], st1["ps"][one] * Imy, atol=1e-16, rtol=1e-11)
+    np.testing.assert_allclose(st2["qx"], st1["qs"][one] * Imy, atol=1e-16, rtol=1e-11)
+    assert np.abs(st2["py"]).max() < 1e-14 * np.abs(st2["px"]).max()
+    # q*_y: the x-vx cell integral of f0 times -(int M(vy)(wc - vy)) over the vy cell
+    x = (i + 0.5)[:, None] * (L / nq) + 0.5 * (L / nq) * g[None, :]
+    vx = (-6.0 + (k + 0.5) * (12.0 / nv))[:, None] + 0.5 * (12.0 / nv) * g[None, :]
+    Ix = (gw[None, :] * 0.5 * (L / nq) * (1 + 0.3 * np.cos(0.5 * x))).sum(1)
+    Ivx = (gw[None, :] * 0.5 * (12.0 / nv) * M(vx)).sum(1)
+    np.testing.assert_allclose(st2["qy"], -Ix * Ivx * Imy1, atol=1e-16, rtol=1e-11)
+
+
+def test_lattice_init_mass_and_symmetry():
+    sp = W.Lattice2DSpec(8, 6, 16, 16, 4 * np.pi, 2 * np.pi, alpha=0.0, quad_order=2)
+    st = O.init_lattice2d(sp)
+    assert st["psi"].sum() == pytest.approx(sp.Lx * sp.Ly, rel=2e-3)
+    assert np.abs(st["px"]).max() < 1e-15 and np.abs(st["py"]).max() < 1e-15     # uniform in space
+    assert np.all(st["Qx"] < sp.Lx) and np.all(st["Qy"] < sp.Ly)

@@ -225,6 +225,39 @@ def random_state_2d(n: int, Lx: float, Ly: float, seed: int = 0, vth: float = 1.
     return {"Qx": Qx, "Qy": Qy, "Px": Px, "Py": Py, "qx": qx, "qy": qy, "px": px, "py": py, "psi": psi}
 
 
+@dataclass(frozen=True)
+class Lattice2DSpec:
+    """A 4D phase-space lattice for 2D2V runs: nqx x nqy positions times
+    nvx x nvy velocities on [0, Lx) x [0, Ly) x [vmin, vmax]^2, of
+    f0 = (1 + alpha cos(kx x + ky y)) exp(-|v|^2 / (2 vth^2)) / (2 pi vth^2)."""
+    nqx: int
+    nqy: int
+    nvx: int
+    nvy: int
+    Lx: float
+    Ly: float
+    vmin: float = -6.0
+    vmax: float = 6.0
+    alpha: float = 0.05
+    kx: float = 0.5
+    ky: float = 0.5
+    vth: float = 1.0
+    quad_order: int = 2
+    decorate: bool = True
+
+    @property
+    def n(self) -> int:
+        return self.nqx * self.nqy * self.nvx * self.nvy
+
+
+def landau_2d(side: int = 64, quad_order: int = 2) -> Lattice2DSpec:
+    """Oblique 2D Landau damping: k = (1/2, 1/2) on [0, 4 pi)^2, alpha 0.05,
+    side^4 decorated particles (64^4 = 16,777,216)."""
+    L = 4 * np.pi
+    return Lattice2DSpec(side, side, side, side, L, L, -6.0, 6.0, 0.05, 2 * np.pi / L, 2 * np.pi / L, 1.0,
+                         quad_order, True)
+
+
 def two_stream_markers(M: int, seed: int = 0, alpha: float = 0.01, L: float = 2 * np.pi,
                        v0: float = 1.0, vth: float = 0.3) -> dict:
     """A seeded random sample of M marker particles of the two-stream f0 of the
