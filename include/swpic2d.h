@@ -64,6 +64,23 @@ typedef struct swpic2d_diag {
     int64_t step;
 } swpic2d_diag;
 
+/* Lattice initialisation (the cluster reading of Sec. 4.2 / Alg. 1 used in
+ * 1D, one dimension up): each cell of an nqx x nqy x nvx x nvy phase-space
+ * lattice on [0, Lx) x [0, Ly) x [vmin, vmax]^2 is the cluster S_a of
+ *   f0 = (1 + alpha cos(kx x + ky y)) exp(-|v|^2 / (2 vth^2)) / (2 pi vth^2);
+ * particle index ((i nqy + j) nvx + k) nvy + l;  Q, P = the cell centre;
+ *   psi* = f0(centre) dx dy dvx dvy
+ *   p*_x = int_cell f0 (Lx/2pi) sin(2pi (Qx - x)/Lx), p*_y likewise  (periodic c)
+ *   q*   = - int_cell f0 (P - p)                                   (Eq. moment-def)
+ * cell integrals by a quad_order^4 Gauss-Legendre rule (1 <= quad_order <= 4),
+ * evaluated in FP64 and stored in the context's precision.                 */
+typedef struct swpic2d_lattice {
+    int32_t nqx, nqy, nvx, nvy;
+    double  vmin, vmax, alpha, kx, ky, vth;
+    int32_t quad_order;
+    int32_t decorate;          /* 0: p*, q* = 0 */
+} swpic2d_lattice;
+
 typedef struct swpic2d_ctx swpic2d_ctx;
 
 /* Validate cfg, allocate the context's own device buffers (charge
@@ -84,6 +101,11 @@ swpic_status swpic2d_bind_state(swpic2d_ctx *ctx, void *const state[9], swpic_st
  * 2^58) and compute the field of the state (deposit, solve, node table).
  * Call after writing the state and before swpic2d_step. */
 swpic_status swpic2d_refresh(swpic2d_ctx *ctx);
+
+/* Synchronous.  Write the lattice state into the bound arrays (the product
+ * nqx nqy nvx nvy must equal the context's particle count) and take its
+ * field (as swpic2d_refresh). */
+swpic_status swpic2d_init_lattice(swpic2d_ctx *ctx, const swpic2d_lattice *spec);
 
 /* Advance n_steps >= 0 leapfrog steps (asynchronous).  The closing half-kick
  * of a step and the opening half-kick of the next share one fused pass over

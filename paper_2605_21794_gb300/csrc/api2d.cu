@@ -334,6 +334,55 @@ swpic_status swpic2d_refresh(swpic2d_ctx *ctx) {
     return SWPIC_OK;
 }
 
+// Gauss-Legendre nodes and weights on [-1, 1] (Newton on the three-term
+// recurrence of P_n), n <= 8: out[0..n) nodes, out[8..8+n) weights.
+static void gauss_legendre(int n, double *out) {
+    for (int k = 0; k < n; ++k) {
+        double z = std::cos(M_PI * (k + 0.75) / (n + 0.5)), pn = 0.0, pm = 0.0, dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            pn = z; pm = 1.0;
+            for (int m = 2; m <= n; ++m) { const double q = ((2.0 * m - 1.0) * z * pn - (m - 1.0) * pm) / m; pm = pn; pn = q; }
+            if (n == 1) { pn = z; pm = 1.0; }
+            dp = n * (z * pn - pm) / (z * z - 1.0);
+            const double dz = pn / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        pn = z; pm = 1.0;
+        for (int m = 2; m <= n; ++m) { const double q = ((2.0 * m - 1.0) * z * pn - (m - 1.0) * pm) / m; pm = pn; pn = q; }
+        dp = n * (z * pn - pm) / (z * z - 1.0);
+        out[k] = -z;
+        out[8 + k] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+swpic_status swpic2d_init_lattice(swpic2d_ctx *ctx, const swpic2d_lattice *spec) {
+    if (!ctx || !spec) return SWPIC_EINVAL;
+    if (!ctx->bound) return fail(ctx, SWPIC_ESTATE, "no state bound");
+    const swpic2d_lattice &f = *spec;
+    if (f.nqx < 1 || f.nqy < 1 || f.nvx < 1 || f.nvy < 1 || f.quad_order < 1 || f.quad_order > 4 ||
+        !(f.vmax > f.vmin) || !(f.vth > 0.0) || !std::isfinite(f.alpha) || !std::isfinite(f.kx) ||
+        !std::isfinite(f.ky))
+        return fail(ctx, SWPIC_EINVAL, "bad lattice");
+    if ((int64_t)f.nqx * f.nqy * f.nvx * f.nvy != ctx->n)
+        return fail(ctx, SWPIC_EINVAL, "nqx nqy nvx nvy must equal the particle count");
+    double gl[16] = {};
+    gauss_legendre(f.quad_order, gl);
+    double *dgl = nullptr;
+    CK2(cudaMalloc(&dgl, sizeof(gl)));
+    cudaError_t e = cudaMemcpyAsync(dgl, gl, sizeof(gl), cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) {
+        swpic2d_lattice g = f;
+        if (!ctx->dec) g.decorate = 0;
+        e = launch_init_lattice(ctx->prec, g, ctx->cfg.Lx, ctx->cfg.Ly, dgl, ctx->st, ctx->stream);
+        ++ctx->launches;
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    cudaFree(dgl);
+    CK2(e);
+    return swpic2d_refresh(ctx);
+}
+
 swpic_status swpic2d_step(swpic2d_ctx *ctx, int32_t n_steps, int32_t diag_every) {
     if (!ctx || n_steps < 0 || diag_every < 0) return SWPIC_EINVAL;
     if (!ctx->ready) return fail(ctx, SWPIC_ESTATE, "call swpic2d_refresh after binding or writing the state");

@@ -549,8 +549,71 @@ __global__ void k_record2d(RecordArgs2d r) {
 }
 
 // ---------------------------------------------------------------------------
+// Lattice initialisation: one thread per particle, cell integrals by the
+// n^4 Gauss-Legendre rule in FP64 (nodes and weights on [-1, 1] in gl[0..n),
+// gl[8..8+n)), stored in the state precision.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double f0_lattice(const swpic2d_lattice &f, double x, double y, double vx, double vy) {
+    return (1.0 + f.alpha * cos(f.kx * x + f.ky * y)) * exp(-(vx * vx + vy * vy) / (2.0 * f.vth * f.vth)) /
+           (2.0 * M_PI * f.vth * f.vth);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_init_lattice2d(swpic2d_lattice f, double Lx, double Ly, const double *gl,
+                                                        PassArgs2d a) {
+    const int64_t n = (int64_t)f.nqx * f.nqy * f.nvx * f.nvy;
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int l = (int)(p % f.nvy), k = (int)((p / f.nvy) % f.nvx);
+    const int j = (int)((p / ((int64_t)f.nvy * f.nvx)) % f.nqy), i = (int)(p / ((int64_t)f.nvy * f.nvx * f.nqy));
+    const double dx = Lx / f.nqx, dy = Ly / f.nqy, dvx = (f.vmax - f.vmin) / f.nvx, dvy = (f.vmax - f.vmin) / f.nvy;
+    const double xc = (i + 0.5) * dx, yc = (j + 0.5) * dy;
+    const double uc = f.vmin + (k + 0.5) * dvx, wc = f.vmin + (l + 0.5) * dvy;
+    double sx = 0.0, sy = 0.0, tx = 0.0, ty = 0.0;
+    if (f.decorate) {
+        const int nq = f.quad_order;
+        for (int r = 0; r < nq; ++r)
+            for (int s = 0; s < nq; ++s)
+                for (int t = 0; t < nq; ++t)
+                    for (int u = 0; u < nq; ++u) {
+                        const double x = xc + 0.5 * dx * gl[r], y = yc + 0.5 * dy * gl[s];
+                        const double vx = uc + 0.5 * dvx * gl[t], vy = wc + 0.5 * dvy * gl[u];
+                        const double wgt = gl[8 + r] * gl[8 + s] * gl[8 + t] * gl[8 + u] * 0.0625 * dx * dy * dvx * dvy;
+                        const double fv = wgt * f0_lattice(f, x, y, vx, vy);
+                        sx += fv * (Lx / (2.0 * M_PI)) * sin(2.0 * M_PI * (xc - x) / Lx);
+                        sy += fv * (Ly / (2.0 * M_PI)) * sin(2.0 * M_PI * (yc - y) / Ly);
+                        tx += -fv * (uc - vx);
+                        ty += -fv * (wc - vy);
+                    }
+    }
+    static_cast<T *>(a.Qx)[p] = (T)xc;
+    static_cast<T *>(a.Qy)[p] = (T)yc;
+    static_cast<T *>(a.Px)[p] = (T)uc;
+    static_cast<T *>(a.Py)[p] = (T)wc;
+    const_cast<T *>(static_cast<const T *>(a.psi))[p] = (T)(f0_lattice(f, xc, yc, uc, wc) * dx * dy * dvx * dvy);
+    if (a.qx) {
+        static_cast<T *>(a.qx)[p] = (T)tx;
+        static_cast<T *>(a.qy)[p] = (T)ty;
+        static_cast<T *>(a.px)[p] = (T)sx;
+        static_cast<T *>(a.py)[p] = (T)sy;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+cudaError_t launch_init_lattice(int prec, const swpic2d_lattice &spec, double Lx, double Ly,
+                                const double *gl, void *const st[9], cudaStream_t s) {
+    PassArgs2d a{};
+    a.Qx = st[0]; a.Qy = st[1]; a.Px = st[2]; a.Py = st[3];
+    a.qx = st[4]; a.qy = st[5]; a.px = st[6]; a.py = st[7]; a.psi = st[8];
+    const int64_t n = (int64_t)spec.nqx * spec.nqy * spec.nvx * spec.nvy;
+    if (n == 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((n + 255) / 256);
+    if (prec == SWPIC_F64) k_init_lattice2d<double><<<grid, 256, 0, s>>>(spec, Lx, Ly, gl, a);
+    else k_init_lattice2d<float><<<grid, 256, 0, s>>>(spec, Lx, Ly, gl, a);
+    return cudaGetLastError();
+}
 size_t pass_smem_bytes(int prec, int nn, bool deposit) {
     const size_t e = (prec == SWPIC_F64) ? 8 : 4;
     return (size_t)nn * 4 * e + (deposit ? (size_t)nn * e : 0);

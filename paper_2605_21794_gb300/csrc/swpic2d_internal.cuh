@@ -69,5 +69,7 @@ cudaError_t launch_solve(int prec, const SolveArgs2d &a, cudaStream_t s, int64_t
 cudaError_t launch_record(const RecordArgs2d &a, cudaStream_t s);
 cudaError_t launch_bound(int prec, const PassArgs2d &a, double *out, int grid, cudaStream_t s);
 const void *pass_kernel(int prec, bool decorated, bool deposit, bool diag);
+cudaError_t launch_init_lattice(int prec, const swpic2d_lattice &spec, double Lx, double Ly,
+                                const double *gl, void *const st[9], cudaStream_t s);
 
 }  // namespace swpic2d

@@ -56,6 +56,12 @@ class swpic2d_config(C.Structure):
                 ("diag_capacity", C.c_int32), ("reserved", C.c_int32)]
 
 
+class swpic2d_lattice(C.Structure):
+    _fields_ = [("nqx", C.c_int32), ("nqy", C.c_int32), ("nvx", C.c_int32), ("nvy", C.c_int32),
+                ("vmin", C.c_double), ("vmax", C.c_double), ("alpha", C.c_double), ("kx", C.c_double),
+                ("ky", C.c_double), ("vth", C.c_double), ("quad_order", C.c_int32), ("decorate", C.c_int32)]
+
+
 class swpic2d_diag(C.Structure):
     _fields_ = [("t", C.c_double), ("mass", C.c_double), ("momentum_x", C.c_double),
                 ("momentum_y", C.c_double), ("kinetic", C.c_double), ("field_energy", C.c_double),
@@ -114,6 +120,7 @@ SIGNATURES = {
     "swpic2d_last_error": (C.c_char_p, [_CTX]),
     "swpic2d_bind_state": (C.c_int, [_CTX, C.POINTER(_P), _P]),
     "swpic2d_refresh": (C.c_int, [_CTX]),
+    "swpic2d_init_lattice": (C.c_int, [_CTX, C.POINTER(swpic2d_lattice)]),
     "swpic2d_step": (C.c_int, [_CTX, C.c_int32, C.c_int32]),
     "swpic2d_diagnostics": (C.c_int, [_CTX, C.POINTER(swpic2d_diag), C.c_int32, C.POINTER(C.c_int32)]),
     "swpic2d_get_field": (C.c_int, [_CTX, _D, _D, _D, _D]),
@@ -480,6 +487,17 @@ def swpic2d_refresh(ctx):
     _check2(load_library().swpic2d_refresh(ctx), ctx)
 
 
+def lattice2d_struct(spec) -> swpic2d_lattice:
+    """swpic2d_lattice from a workloads.Lattice2DSpec."""
+    return swpic2d_lattice(int(spec.nqx), int(spec.nqy), int(spec.nvx), int(spec.nvy), float(spec.vmin),
+                           float(spec.vmax), float(spec.alpha), float(spec.kx), float(spec.ky), float(spec.vth),
+                           int(spec.quad_order), int(bool(spec.decorate)))
+
+
+def swpic2d_init_lattice(ctx, spec: swpic2d_lattice):
+    _check2(load_library().swpic2d_init_lattice(ctx, C.byref(spec)), ctx)
+
+
 def swpic2d_step(ctx, n_steps, diag_every=0):
     _check2(load_library().swpic2d_step(ctx, int(n_steps), int(diag_every)), ctx)
 
@@ -571,6 +589,11 @@ class Simulation2D:
             v[: self.n].copy_(torch.from_numpy(np.ascontiguousarray(src)).to(self.dtype))
         torch.cuda.synchronize()
         swpic2d_refresh(self.ctx)
+
+    def init_lattice(self, spec):
+        """Lattice state of a workloads.Lattice2DSpec, built on the device
+        (swpic2d_init_lattice), and its field."""
+        swpic2d_init_lattice(self.ctx, lattice2d_struct(spec))
 
     def state(self):
         swpic2d_synchronize(self.ctx)

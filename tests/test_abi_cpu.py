@@ -146,3 +146,22 @@ def test_2d_create_rejects_bad_configs_before_touching_the_device(lib):
     assert lib.swpic2d_step(None, 1, 0) == swpic.SWPIC_EINVAL
     assert lib.swpic2d_refresh(None) == swpic.SWPIC_EINVAL
     lib.swpic2d_destroy(None)
+
+
+def test_2d_lattice_struct_layout_matches_c(tmp_path):
+    from paper_2605_21794_gb300 import swpic
+    src = tmp_path / "lat2d.c"
+    src.write_text('''
+#include <stdio.h>
+#include <stddef.h>
+#include "swpic2d.h"
+int main(void) {
+  printf("%zu %zu %zu\\n", sizeof(swpic2d_lattice), offsetof(swpic2d_lattice, vmin),
+         offsetof(swpic2d_lattice, decorate));
+  return 0;
+}''')
+    exe = tmp_path / "lat2d"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == [C.sizeof(swpic.swpic2d_lattice), swpic.swpic2d_lattice.vmin.offset,
+                   swpic.swpic2d_lattice.decorate.offset]

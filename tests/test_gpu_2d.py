@@ -208,3 +208,42 @@ def test_fp32_point_particles_and_largest_fp32_mesh():
     _compare(got, ref, Lx, Ly, 1e-5, KEYS[:4])
     for c in (1, 2, 3, 4, 5, 7):
         assert rel_max(diag[:, c], ref["diag"][:, c]) < 1e-4, c
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_lattice_init_matches_oracle(precision):
+    """The device builds the lattice state itself (n^4 Gauss rule in FP64)."""
+    need_gpu()
+    sp = W.Lattice2DSpec(8, 4, 12, 10, 4 * np.pi, 2 * np.pi, -6.0, 6.0, 0.2, 0.5, 1.0, 1.0, 3, True)
+    sim = _sim(sp.Lx, sp.Ly, 16, 8, 0.1, sp.n, precision)
+    try:
+        sim.init_lattice(sp)
+        got = sim.state()
+    finally:
+        sim.close()
+    ref = _cast(O.init_lattice2d(sp), precision)
+    tol = 1e-13 if precision == 64 else 0.0
+    for k in ("Qx", "Qy", "Px", "Py", "psi", "qx", "qy", "px", "py"):
+        s = np.abs(ref[k]).max()
+        assert np.abs(got[k] - ref[k]).max() <= max(tol * s, 0.0 if precision == 64 else 2e-7 * s), k
+
+
+def test_oblique_landau_damping_rate():
+    """Linear Landau damping of the oblique mode k = (1/2, 1/2), |k| = 1/sqrt 2,
+    from the decorated lattice start: the fitted decay rate of E_amp matches
+    the kinetic dispersion root of a Maxwellian at |k| (an isotropic plasma
+    damps an oblique mode as a 1D one of the same |k|) to within 5%."""
+    need_gpu()
+    from workloads import physics as ph
+    sp = W.Lattice2DSpec(32, 32, 48, 48, 4 * np.pi, 4 * np.pi, -6.0, 6.0, 0.01, 0.5, 0.5, 1.0, 2, True)
+    sim = _sim(sp.Lx, sp.Ly, 32, 32, 0.05, sp.n, 64)
+    try:
+        sim.init_lattice(sp)
+        sim.step(260, 1)
+        d = sim.diagnostics()
+    finally:
+        sim.close()
+    kk = np.sqrt(0.5)
+    root = ph.landau_root(kk, 1.0 + 0.5 * kk * kk * 3 - 0.2j)
+    g, _, _ = ph.rate_fit(d[:, 0], d[:, 7], 1.5, 12.0, min_sep=1.0)
+    assert g == pytest.approx(root.imag, rel=0.05), (g, root)
