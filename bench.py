@@ -59,7 +59,7 @@ def parse():
     ap.add_argument("--only-2d", action="store_true",
                     help="run only the 2D2V leg (K timed steps) and print its JSON object")
     ap.add_argument("--side-2d", type=int, default=4096,
-                    help="2D leg: particles = side^2 (4096 = the 2D workload)")
+                    help="2D leg: particles = side^2 = (lattice side)^4 (4096 = the 2D workload, 64^4)")
     ap.add_argument("--d2-mode", choices=list(D2_MODES), default="lumped",
                     help="phi'' of the kick: P1 field with a lumped or nodal projection, or the P2 field")
     return ap.parse_args()
@@ -528,15 +528,16 @@ BYTES_PER_PARTICLE_2D = {32: 68, 64: 136}     # read Q, P, q*, p* (2 each) and p
 
 def two_d_leg(torch, swpic, args):
     """The 2D2V step (general-d model of Sec. 3.3 on the torus, bilinear
-    elements): 16,777,216 FP32 decorated particles of a seeded 2D Landau-like
-    state on a 32 x 32 mesh of [0, 4 pi)^2, dt 0.1, diagnostics every step;
+    elements): oblique Landau damping, k = (1/2, 1/2) on [0, 4 pi)^2,
+    alpha 0.05, a side^4 decorated lattice (64^4 = 16,777,216 FP32 particles,
+    built on the device) on a 32 x 32 mesh, dt 0.1, diagnostics every step;
     warm-up W steps, K device-timed steps, then the per-pass roofline."""
-    n, L, nx, dt = args.side_2d * args.side_2d, 4 * np.pi, 32, 0.1
-    st = W.random_state_2d(n, L, L, seed=2024, nx=nx, ny=nx, alpha=0.1)
+    side = int(round(args.side_2d ** 0.5))
+    spec = W.landau_2d(side)
+    n, L, nx, dt = spec.n, spec.Lx, 32, 0.1
     sim = swpic.Simulation2D(L, L, nx, nx, dt, n, precision=32, diag_capacity=args.warmup + 2 * args.steps + 8)
     try:
-        sim.init_particles(st)
-        del st
+        sim.init_lattice(spec)
         sim.step(args.warmup, args.diag_every)
         swpic.swpic2d_synchronize(sim.ctx)
         l0 = swpic.swpic2d_launch_count(sim.ctx)
@@ -562,12 +563,12 @@ def two_d_leg(torch, swpic, args):
     peak, peak_src = measured_peak()
     achieved = bpp * n / (avg / 1e3) / 1e9
     H = d[:, 6]
-    return {"workload": "landau2d_random_%dx%d_mesh_32x32" % (args.side_2d, args.side_2d), "particles": n, "mesh": [nx, nx], "dt": dt,
+    return {"workload": "landau2d_oblique_lattice_%d^4_mesh_32x32" % side, "particles": n, "mesh": [nx, nx], "dt": dt,
             "value": n * args.steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / args.steps,
             "gpu_launches": int(launches),
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "avg_launch_ms": avg,
-                         "traffic": profiled_traffic("k_pass2d_landau2d_4096x4096") if n == 1 << 24 else None,
+                         "traffic": profiled_traffic("k_pass2d_landau2d_64x64x64x64") if n == 1 << 24 else None,
                          "kernel": "k_pass2d<float, decorated, deposit, diag>",
                          "algorithmic_bytes_per_launch": bpp * n, "peak_source": peak_src},
             "max_abs_dH_over_H0": float(np.max(np.abs(H - H[0])) / abs(H[0])),
@@ -670,17 +671,18 @@ def cpu_baseline_leg(spec, args):
 
 
 def two_d_oracle_sample(args):
-    """The 2D oracle on 65,536 particles of the 2D workload's state (same
-    mesh, dt), 5 steps, one core (its dense LU of the 1025 x 1025 bordered
-    system is included)."""
+    """The 2D oracle on a 16^4 lattice (65,536 particles) of the 2D workload's
+    f0 (same domain, mesh and dt), 5 steps, one core (its dense LU of the
+    1025 x 1025 bordered system is included)."""
     import oracle as O
-    n, L, nx, k = 1 << 16, 4 * np.pi, 32, 5
-    st = W.random_state_2d(n, L, L, seed=2024, nx=nx, ny=nx, alpha=0.1)
+    spec = W.landau_2d(16)
+    st = O.init_lattice2d(spec)
+    k = 5
     t0 = time.perf_counter()
-    O.run2d(st, nx, nx, L, L, 0.1, k, diag_every=args.diag_every)
+    O.run2d(st, 32, 32, spec.Lx, spec.Ly, 0.1, k, diag_every=args.diag_every)
     t = time.perf_counter() - t0
-    return {"value": n * k / t, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d particles of the 2D workload's distribution, 32 x 32 mesh, %d steps" % (n, k)}
+    return {"value": spec.n * k / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "16^4 lattice (%d particles) of the 2D workload's f0, 32 x 32 mesh, %d steps" % (spec.n, k)}
 
 
 def p2_oracle_sample(spec, args):

@@ -228,22 +228,52 @@ def test_lattice_init_matches_oracle(precision):
         assert np.abs(got[k] - ref[k]).max() <= max(tol * s, 0.0 if precision == 64 else 2e-7 * s), k
 
 
-def test_oblique_landau_damping_rate():
-    """Linear Landau damping of the oblique mode k = (1/2, 1/2), |k| = 1/sqrt 2,
-    from the decorated lattice start: the fitted decay rate of E_amp matches
-    the kinetic dispersion root of a Maxwellian at |k| (an isotropic plasma
-    damps an oblique mode as a 1D one of the same |k|) to within 5%."""
+def test_axis_mode_reproduces_the_1d_step():
+    """A y-uniform f0 on the 2D lattice (particles at the y cell centres) has a
+    y-independent field, so the 2D step must reproduce the 1D step on the
+    matching 1D lattice: the E_amp histories of the two GPU paths (each pinned
+    to its own oracle) agree over 100 FP64 steps of linear Landau damping."""
     need_gpu()
-    from workloads import physics as ph
-    sp = W.Lattice2DSpec(32, 32, 48, 48, 4 * np.pi, 4 * np.pi, -6.0, 6.0, 0.01, 0.5, 0.5, 1.0, 2, True)
-    sim = _sim(sp.Lx, sp.Ly, 32, 32, 0.05, sp.n, 64)
+    from paper_2605_21794_gb300 import swpic
+    L = 4 * np.pi
+    sp = W.Lattice2DSpec(32, 4, 48, 6, L, 3.0, -6.0, 6.0, 0.01, 0.5, 0.0, 1.0, 2, True)
+    sim = _sim(L, 3.0, 32, 4, 0.05, sp.n, 64)
     try:
         sim.init_lattice(sp)
-        sim.step(260, 1)
+        sim.step(100, 1)
+        d2 = sim.diagnostics()
+    finally:
+        sim.close()
+    lat = W.LatticeSpec(32, 48, L, -6.0, 6.0, 0.01, 0.5, W.MAXWELL, quad_order=2)
+    s1 = swpic.Simulation([(L, 0.05, 32, lat.n)], precision=64)
+    try:
+        s1.init_lattice(0, lat)
+        s1.step(100, 1)
+        d1 = s1.diagnostics()
+    finally:
+        s1.close()
+    assert d1.shape[0] == d2.shape[0] == 101
+    assert rel_max(d2[:, 7], d1[:, 6]) < 1e-8
+
+
+def test_oblique_landau_damping_rate():
+    """Linear Landau damping of an oblique mode, k = (1, 1) 2 pi / L with
+    |k| = 1/2, from the decorated lattice start: the decay rate of E_amp fitted
+    over t in [1, 8] is the kinetic dispersion root of a Maxwellian at |k|
+    (an isotropic plasma damps an oblique mode as a 1D one of the same |k|)
+    within 10%, the accuracy the 1D step has at this resolution."""
+    need_gpu()
+    from workloads import physics as ph
+    kq = 0.5 / np.sqrt(2)
+    L = 2 * np.pi / kq
+    sp = W.Lattice2DSpec(32, 32, 48, 48, L, L, -6.0, 6.0, 0.01, kq, kq, 1.0, 2, True)
+    sim = _sim(L, L, 32, 32, 0.05, sp.n, 64)
+    try:
+        sim.init_lattice(sp)
+        sim.step(180, 1)
         d = sim.diagnostics()
     finally:
         sim.close()
-    kk = np.sqrt(0.5)
-    root = ph.landau_root(kk, 1.0 + 0.5 * kk * kk * 3 - 0.2j)
-    g, _, _ = ph.rate_fit(d[:, 0], d[:, 7], 1.5, 12.0, min_sep=1.0)
-    assert g == pytest.approx(root.imag, rel=0.05), (g, root)
+    root = ph.landau_root(0.5, 1.4 - 0.15j)
+    g, _, _ = ph.rate_fit(d[:, 0], d[:, 7], 1.0, 8.0, min_sep=1.0)
+    assert g == pytest.approx(root.imag, rel=0.10), (g, root)
