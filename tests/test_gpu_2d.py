@@ -229,31 +229,39 @@ def test_lattice_init_matches_oracle(precision):
 
 
 def test_axis_mode_reproduces_the_1d_step():
-    """A y-uniform f0 on the 2D lattice (particles at the y cell centres) has a
-    y-independent field, so the 2D step must reproduce the 1D step on the
-    matching 1D lattice: the E_amp histories of the two GPU paths (each pinned
-    to its own oracle) agree over 100 FP64 steps of linear Landau damping."""
+    """A y-uniform f0 on a lattice whose y spacing is the mesh spacing keeps
+    the field y-independent (rows of particles deposit uniformly, and their
+    y-dipoles cancel along each row), so every particle's x-motion is that of
+    a 1D particle: the 2D step must reproduce the 1D step run on the rows
+    merged into 1D particles (weights summed over y and vy, divided by Ly).
+    Both GPU paths (each pinned to its own oracle) advance 100 FP64 steps of
+    linear Landau damping from the oracle's lattice; E_amp agrees."""
     need_gpu()
     from paper_2605_21794_gb300 import swpic
-    L = 4 * np.pi
-    sp = W.Lattice2DSpec(32, 4, 48, 6, L, 3.0, -6.0, 6.0, 0.01, 0.5, 0.0, 1.0, 2, True)
-    sim = _sim(L, 3.0, 32, 4, 0.05, sp.n, 64)
+    L, Ly, nqx, nqy, nvx, nvy = 4 * np.pi, 3.0, 32, 4, 48, 6
+    sp = W.Lattice2DSpec(nqx, nqy, nvx, nvy, L, Ly, -6.0, 6.0, 0.01, 0.5, 0.0, 1.0, 2, True)
+    st2 = O.init_lattice2d(sp)
+    sim = _sim(L, Ly, 32, nqy, 0.05, sp.n, 64)
     try:
-        sim.init_lattice(sp)
+        sim.init_particles(st2)
         sim.step(100, 1)
         d2 = sim.diagnostics()
     finally:
         sim.close()
-    lat = W.LatticeSpec(32, 48, L, -6.0, 6.0, 0.01, 0.5, W.MAXWELL, quad_order=2)
-    s1 = swpic.Simulation([(L, 0.05, 32, lat.n)], precision=64)
+    shape = (nqx, nqy, nvx, nvy)
+    merged = lambda k: st2[k].reshape(shape).sum(axis=(1, 3)).ravel() / Ly
+    st1 = {"Q": st2["Qx"].reshape(shape)[:, 0, :, 0].ravel(), "P": st2["Px"].reshape(shape)[:, 0, :, 0].ravel(),
+           "psi": merged("psi"), "qs": merged("qx"), "ps": merged("px")}
+    s1 = swpic.Simulation([(L, 0.05, 32, len(st1["Q"]))], precision=64)
     try:
-        s1.init_lattice(0, lat)
+        s1.init_particles(st1)
         s1.step(100, 1)
         d1 = s1.diagnostics()
     finally:
         s1.close()
     assert d1.shape[0] == d2.shape[0] == 101
     assert rel_max(d2[:, 7], d1[:, 6]) < 1e-8
+    assert rel_max(d2[:, 5], Ly * d1[:, 4]) < 1e-8          # W_2D = Ly W_1D
 
 
 def test_oblique_landau_damping_rate():
