@@ -98,8 +98,11 @@ swpic_status swpic2d_bind_state(swpic2d_ctx *ctx, void *const state[9], swpic_st
 
 /* Synchronous.  Take the fixed-point unit of the charge accumulator from
  * the bound state (sum psi* + 2 sum |p*_x|/hx + 2 sum |p*_y|/hy maps to
- * 2^58) and compute the field of the state (deposit, solve, node table).
- * Call after writing the state and before swpic2d_step. */
+ * 2^58 in FP64 contexts, 2^54 in FP32 ones; the limit is 2^62, and the
+ * decorations p* grow in time) and compute the field of the state (deposit,
+ * solve, node table).  Call after writing the state and before
+ * swpic2d_step; a run whose decorations outgrow the headroom reports
+ * SWPIC_ENUMERIC, and a refresh takes a new unit. */
 swpic_status swpic2d_refresh(swpic2d_ctx *ctx);
 
 /* Synchronous.  Write the lattice state into the bound arrays (the product

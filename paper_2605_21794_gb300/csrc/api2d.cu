@@ -16,7 +16,13 @@
 using namespace swpic2d;
 
 namespace {
-constexpr int kFixedBits2d = 58;     // the deposit bound maps to 2^58 units (2^62 limit)
+// The deposit bound of the state at refresh maps to 2^58 units (FP64) or
+// 2^54 units (FP32); the accumulator's limit is 2^62.  The dipole weights p*
+// grow in time (dp*/dt = -q*, the shear of nearby characteristics), so the
+// bound grows too: FP32 runs keep 2^8 of headroom for it, at a quantum far
+// below FP32 resolution; FP64 runs keep 2^4 and a quantum of 2^-58 of the bound.
+constexpr int kFixedBits2dF64 = 58;
+constexpr int kFixedBits2dF32 = 54;
 }
 
 struct swpic2d_ctx {
@@ -317,8 +323,9 @@ swpic_status swpic2d_refresh(swpic2d_ctx *ctx) {
         CK2(cudaStreamSynchronize(ctx->stream));
     }
     if (!std::isfinite(m)) return fail(ctx, SWPIC_ENUMERIC, "non-finite particle weights");
-    int k = kFixedBits2d;
-    if (m > 0.0) k = kFixedBits2d - (int)std::ceil(std::log2(m));
+    const int bits = (ctx->prec == SWPIC_F64) ? kFixedBits2dF64 : kFixedBits2dF32;
+    int k = bits;
+    if (m > 0.0) k = bits - (int)std::ceil(std::log2(m));
     k = std::max(-1000, std::min(1000, k));
     ctx->fx_scale = std::ldexp(1.0, k);
     ctx->fx_inv = std::ldexp(1.0, -k);
