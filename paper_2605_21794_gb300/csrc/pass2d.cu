@@ -284,6 +284,43 @@ __device__ void solve_tail_f32(const SolveArgs2d &s, unsigned char *smem) {
 }
 
 // ---------------------------------------------------------------------------
+// Warp-aggregated deposit of one particle per lane into its cell's four
+// corner nodes.  Lanes with the same cell in consecutive lanes form a segment
+// (an ordered or cold plasma); a segmented suffix sum gives the segment's
+// first lane the segment's four totals, and only that lane adds them to the
+// shared mesh.  When no lane shares its cell with the lane before (a
+// disordered plasma) the shuffles are skipped.  key < 0: an empty slot.  All
+// 32 lanes must call this.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void warp_deposit4(int key, T w0, T w1, T w2, T w3, T *mesh, int nx, int ny,
+                                              int lognx) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int prev = __shfl_up_sync(full, key, 1);
+    const bool head = (lane == 0) || (prev != key);
+    const unsigned heads = __ballot_sync(full, head);
+    if (heads != full) {
+        const unsigned above = (lane == 31) ? 0u : (heads & (0xffffffffu << (lane + 1)));
+        const int seg_end = above ? (__ffs(above) - 2) : 31;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const T b0 = __shfl_down_sync(full, w0, off), b1 = __shfl_down_sync(full, w1, off);
+            const T b2 = __shfl_down_sync(full, w2, off), b3 = __shfl_down_sync(full, w3, off);
+            if (lane + off <= seg_end) { w0 += b0; w1 += b1; w2 += b2; w3 += b3; }
+        }
+    }
+    if (head && key >= 0) {
+        const int di = key & (nx - 1), dj = key >> lognx;
+        const int di1 = (di + 1) & (nx - 1), dj1 = (dj + 1) & (ny - 1);
+        atomicAdd(mesh + (dj << lognx) + di, w0);
+        atomicAdd(mesh + (dj << lognx) + di1, w1);
+        atomicAdd(mesh + (dj1 << lognx) + di, w2);
+        atomicAdd(mesh + (dj1 << lognx) + di1, w3);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // The fused particle pass
 // ---------------------------------------------------------------------------
 template <typename T> struct Part { T x, y, vx, vy, w, sx, sy, rx, ry; };
@@ -321,16 +358,27 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
         if (DEC) { c.sx = qx[p]; c.sy = qy[p]; c.rx = px[p]; c.ry = py[p]; }
         else { c.sx = c.sy = c.rx = c.ry = T(0); }
     };
+    // the trip count is warp-uniform (the deposit is a warp operation); lanes
+    // past the end carry empty deposit slots
+    const int lognx = __ffs(nx) - 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t lane64 = threadIdx.x & 31;
     Part<T> cur;
-    if (p < a.n) load(p, cur);
-    for (; p < a.n; p += stride) {
+    bool have = p < a.n;
+    if (have) load(p, cur);
+    for (; p - lane64 < a.n; p += stride) {
         Part<T> nxt;
-        if (p + stride < a.n) load(p + stride, nxt);
+        const bool nxt_have = p + stride < a.n;
+        if (nxt_have) load(p + stride, nxt);
         T x = cur.x, y = cur.y, vx = cur.vx, vy = cur.vy, sx = cur.sx, sy = cur.sy, rx = cur.rx, ry = cur.ry;
         const T w = cur.w;
+        const bool valid = have;
         cur = nxt;
+        have = nxt_have;
+        int dkey = -1;
+        T d0 = T(0), d1 = T(0), d2 = T(0), d3 = T(0);
+        if (valid) {
         // grad phi_h and H_ik = d_k g_i at Q from the four corners of the cell
         T xi, eta;
         const int i = cell_of(x, ihx, cmx, xi), j = cell_of(y, ihy, cmy, eta);
@@ -382,11 +430,15 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
             const int di1 = (di + 1 == nx) ? 0 : di + 1, dj1 = (dj + 1 == ny) ? 0 : dj + 1;
             const T ou = T(1) - u, ov = T(1) - v;
             const T ax = DEC ? rx * ihx : T(0), ay = DEC ? ry * ihy : T(0);
-            atomicAdd(mesh + dj * nx + di, w * ou * ov + ax * ov + ay * ou);
-            atomicAdd(mesh + dj * nx + di1, w * u * ov - ax * ov + ay * u);
-            atomicAdd(mesh + dj1 * nx + di, w * ou * v + ax * v - ay * ou);
-            atomicAdd(mesh + dj1 * nx + di1, w * u * v - ax * v - ay * u);
+            dkey = (dj << lognx) + di;
+            d0 = w * ou * ov + ax * ov + ay * ou;
+            d1 = w * u * ov - ax * ov + ay * u;
+            d2 = w * ou * v + ax * v - ay * ou;
+            d3 = w * u * v - ax * v - ay * u;
+            (void)di1; (void)dj1;
         }
+        }
+        if (DEP) warp_deposit4<T>(dkey, d0, d1, d2, d3, mesh, nx, ny, lognx);
     }
     __syncthreads();
     if (DEP) {
