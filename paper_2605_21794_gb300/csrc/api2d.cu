@@ -205,8 +205,8 @@ swpic_status swpic2d_create(const swpic2d_config *cfg, int64_t n_particles, swpi
     ctx->nn = nn;
     ctx->tpb = c.threads_per_block ? c.threads_per_block : 256;
     ctx->cap = c.diag_capacity ? c.diag_capacity : 4096;
-    ctx->smem_dep = pass_smem_bytes(ctx->prec, nn, true);
-    ctx->smem_nodep = pass_smem_bytes(ctx->prec, nn, false);
+    ctx->smem_dep = pass_smem_bytes(ctx->prec, c.nx, c.ny, true);
+    ctx->smem_nodep = pass_smem_bytes(ctx->prec, c.nx, c.ny, false);
     const size_t es = (ctx->prec == SWPIC_F64) ? 8 : 4;
     const int ntw = std::max(c.nx, c.ny);
     bool ok = true;

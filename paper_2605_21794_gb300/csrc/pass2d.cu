@@ -311,12 +311,12 @@ __device__ __forceinline__ void warp_deposit4(int key, T w0, T w1, T w2, T w3, T
         }
     }
     if (head && key >= 0) {
-        const int di = key & (nx - 1), dj = key >> lognx;
+        const int di = key & (nx - 1), dj = key >> lognx, rs = nx + 1;      // padded rows
         const int di1 = (di + 1) & (nx - 1), dj1 = (dj + 1) & (ny - 1);
-        atomicAdd(mesh + (dj << lognx) + di, w0);
-        atomicAdd(mesh + (dj << lognx) + di1, w1);
-        atomicAdd(mesh + (dj1 << lognx) + di, w2);
-        atomicAdd(mesh + (dj1 << lognx) + di1, w3);
+        atomicAdd(mesh + dj * rs + di, w0);
+        atomicAdd(mesh + dj * rs + di1, w1);
+        atomicAdd(mesh + dj1 * rs + di, w2);
+        atomicAdd(mesh + dj1 * rs + di1, w3);
     }
 }
 
@@ -330,13 +330,19 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
     using T4 = typename V4<T>::type;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ double s_red[32];
-    const int nx = a.nx, ny = a.ny, nn = nx * ny;
+    // table and mesh rows are padded to nx + 1 entries, so that particles
+    // stacked in y (an ordered or cold plasma) do not all hit one bank
+    const int nx = a.nx, ny = a.ny, nn = nx * ny, rs = nx + 1, lgx = __ffs(nx) - 1;
     T4 *tab = reinterpret_cast<T4 *>(smem);
-    T *mesh = reinterpret_cast<T *>(smem + (size_t)nn * sizeof(T4));
+    T *mesh = reinterpret_cast<T *>(smem + (size_t)rs * ny * sizeof(T4));
     const T4 *gtab = reinterpret_cast<const T4 *>(a.table);
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
-        tab[k] = gtab[k];
-        if (DEP) mesh[k] = T(0);
+        const int pk = (k >> lgx) * rs + (k & (nx - 1));
+        tab[pk] = gtab[k];
+        if (DEP) {
+            mesh[pk] = T(0);
+            if ((k & (nx - 1)) == 0) mesh[pk + nx] = T(0);      // the pad entry
+        }
     }
     __syncthreads();
 
@@ -383,7 +389,7 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
         T xi, eta;
         const int i = cell_of(x, ihx, cmx, xi), j = cell_of(y, ihy, cmy, eta);
         const int i1 = (i + 1 == nx) ? 0 : i + 1, j1 = (j + 1 == ny) ? 0 : j + 1;
-        const T4 c00 = tab[j * nx + i], c10 = tab[j * nx + i1], c01 = tab[j1 * nx + i], c11 = tab[j1 * nx + i1];
+        const T4 c00 = tab[j * rs + i], c10 = tab[j * rs + i1], c01 = tab[j1 * rs + i], c11 = tab[j1 * rs + i1];
         const T oe = T(1) - eta, ox = T(1) - xi;
         const T ex = ((c10.x - c00.x) * oe + (c11.x - c01.x) * eta) * ihx;
         const T ey = ((c01.x - c00.x) * ox + (c11.x - c10.x) * xi) * ihy;
@@ -443,7 +449,7 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
     __syncthreads();
     if (DEP) {
         for (int k = threadIdx.x; k < nn; k += blockDim.x) {
-            const T v = mesh[k];
+            const T v = mesh[(k >> lgx) * rs + (k & (nx - 1))];
             if (v != T(0)) atomicAdd(a.acc + k, to_fixed(v, a.fx_scale, a.err));
         }
     }
@@ -666,9 +672,9 @@ cudaError_t launch_init_lattice(int prec, const swpic2d_lattice &spec, double Lx
     else k_init_lattice2d<float><<<grid, 256, 0, s>>>(spec, Lx, Ly, gl, a);
     return cudaGetLastError();
 }
-size_t pass_smem_bytes(int prec, int nn, bool deposit) {
-    const size_t e = (prec == SWPIC_F64) ? 8 : 4;
-    return (size_t)nn * 4 * e + (deposit ? (size_t)nn * e : 0);
+size_t pass_smem_bytes(int prec, int nx, int ny, bool deposit) {
+    const size_t e = (prec == SWPIC_F64) ? 8 : 4, rows = (size_t)(nx + 1) * ny;   // padded rows
+    return rows * 4 * e + (deposit ? rows * e : 0);
 }
 
 template <typename T>

@@ -62,7 +62,7 @@ struct PassArgs2d {
     SolveArgs2d solve;
 };
 
-size_t pass_smem_bytes(int prec, int nn, bool deposit);
+size_t pass_smem_bytes(int prec, int nx, int ny, bool deposit);
 cudaError_t launch_pass(int prec, bool decorated, bool deposit, bool diag, const PassArgs2d &a, int grid,
                         int tpb, size_t smem, cudaStream_t s);
 cudaError_t launch_solve(int prec, const SolveArgs2d &a, cudaStream_t s, int64_t *launches);
