@@ -68,7 +68,8 @@ typedef struct swpic2d_diag {
  * 1D, one dimension up): each cell of an nqx x nqy x nvx x nvy phase-space
  * lattice on [0, Lx) x [0, Ly) x [vmin, vmax]^2 is the cluster S_a of
  *   f0 = (1 + alpha cos(kx x + ky y)) exp(-|v|^2 / (2 vth^2)) / (2 pi vth^2);
- * particle index ((i nqy + j) nvx + k) nvy + l;  Q, P = the cell centre;
+ * particle index ((k nvy + l) nqy + j) nqx + i (positions fastest, so the
+ * lanes of a warp sit in neighbouring cells);  Q, P = the cell centre;
  *   psi* = f0(centre) dx dy dvx dvy
  *   p*_x = int_cell f0 (Lx/2pi) sin(2pi (Qx - x)/Lx), p*_y likewise  (periodic c)
  *   q*   = - int_cell f0 (P - p)                                   (Eq. moment-def)

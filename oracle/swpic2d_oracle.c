@@ -441,8 +441,9 @@ int or2d_run(int64_t n, double *Qx, double *Qy, double *Px, double *Py, double *
 /* ------------------------------------------------------------------------ */
 /* Lattice initialisation in 2D2V: the reading of Sec. 4.2 / Alg. 1 used in   */
 /* 1D, one dimension up.  Each cell of a 4D phase-space lattice is the        */
-/* cluster S_a of the continuum f0; particle index ((i nqy + j) nvx + k) nvy  */
-/* + l;  Q = cell centre in (x, y), P = cell centre in (vx, vy);              */
+/* cluster S_a of the continuum f0; particle index ((k nvy + l) nqy + j) nqx  */
+/* + i (positions fastest);  Q = cell centre in (x, y), P = cell centre in     */
+/* (vx, vy);                                                                  */
 /*   psi*  = f0(centre) dx dy dvx dvy                        (midpoint)        */
 /*   p*_x  = int_cell f0 (Lx/2pi) sin(2pi (Qx - x)/Lx)   (periodic c, Sec. 4.2) */
 /*   p*_y  = int_cell f0 (Ly/2pi) sin(2pi (Qy - y)/Ly)                         */
@@ -472,7 +473,7 @@ int or2d_init_lattice(int32_t nqx, int32_t nqy, int32_t nvx, int32_t nvy, double
         for (int32_t j = 0; j < nqy; ++j)
             for (int32_t k = 0; k < nvx; ++k)
                 for (int32_t l = 0; l < nvy; ++l) {
-                    const int64_t a = (((int64_t)i * nqy + j) * nvx + k) * nvy + l;
+                    const int64_t a = (((int64_t)k * nvy + l) * nqy + j) * nqx + i;
                     const double xc = (i + 0.5) * dx, yc = (j + 0.5) * dy;
                     const double uc = vmin + (k + 0.5) * dvx, wc = vmin + (l + 0.5) * dvy;
                     Qx[a] = xc; Qy[a] = yc; Px[a] = uc; Py[a] = wc;

@@ -622,8 +622,10 @@ __global__ void __launch_bounds__(256) k_init_lattice2d(swpic2d_lattice f, doubl
     const int64_t n = (int64_t)f.nqx * f.nqy * f.nvx * f.nvy;
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const int l = (int)(p % f.nvy), k = (int)((p / f.nvy) % f.nvx);
-    const int j = (int)((p / ((int64_t)f.nvy * f.nvx)) % f.nqy), i = (int)(p / ((int64_t)f.nvy * f.nvx * f.nqy));
+    // positions fastest: the lanes of a warp lie in neighbouring cells of one
+    // row (distinct nodes, no shared-memory bank conflicts)
+    const int i = (int)(p % f.nqx), j = (int)((p / f.nqx) % f.nqy);
+    const int l = (int)((p / ((int64_t)f.nqx * f.nqy)) % f.nvy), k = (int)(p / ((int64_t)f.nqx * f.nqy * f.nvy));
     const double dx = Lx / f.nqx, dy = Ly / f.nqy, dvx = (f.vmax - f.vmin) / f.nvx, dvy = (f.vmax - f.vmin) / f.nvy;
     const double xc = (i + 0.5) * dx, yc = (j + 0.5) * dy;
     const double uc = f.vmin + (k + 0.5) * dvx, wc = f.vmin + (l + 0.5) * dvy;

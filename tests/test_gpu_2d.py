@@ -248,9 +248,9 @@ def test_axis_mode_reproduces_the_1d_step():
         d2 = sim.diagnostics()
     finally:
         sim.close()
-    shape = (nqx, nqy, nvx, nvy)
-    merged = lambda k: st2[k].reshape(shape).sum(axis=(1, 3)).ravel() / Ly
-    st1 = {"Q": st2["Qx"].reshape(shape)[:, 0, :, 0].ravel(), "P": st2["Px"].reshape(shape)[:, 0, :, 0].ravel(),
+    shape = (nvx, nvy, nqy, nqx)                   # particle index ((k nvy + l) nqy + j) nqx + i
+    merged = lambda k: st2[k].reshape(shape).sum(axis=(1, 2)).ravel() / Ly
+    st1 = {"Q": st2["Qx"].reshape(shape)[:, 0, 0, :].ravel(), "P": st2["Px"].reshape(shape)[:, 0, 0, :].ravel(),
            "psi": merged("psi"), "qs": merged("qx"), "ps": merged("px")}
     s1 = swpic.Simulation([(L, 0.05, 32, len(st1["Q"]))], precision=64)
     try:

@@ -228,7 +228,7 @@ def test_lattice_init_with_ky_zero_factors_into_the_1d_init():
     dy, dvy = Ly / 2, 12.0 / 6
     M = lambda v: np.exp(-v * v / 2) / np.sqrt(2 * np.pi)
     a = np.arange(sp2.n)
-    i, j, k, l = a // (2 * nv * 6), (a // (nv * 6)) % 2, (a // 6) % nv, a % 6
+    i, j, l, k = a % nq, (a // nq) % 2, (a // (2 * nq)) % 6, a // (2 * nq * 6)    # positions fastest
     one = i * nv + k                                        # the 1D particle of (i, k)
     wc = -6.0 + (l + 0.5) * dvy
     vy = wc[:, None] + 0.5 * dvy * g[None, :]
