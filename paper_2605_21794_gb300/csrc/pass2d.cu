@@ -284,43 +284,6 @@ __device__ void solve_tail_f32(const SolveArgs2d &s, unsigned char *smem) {
 }
 
 // ---------------------------------------------------------------------------
-// Warp-aggregated deposit of one particle per lane into its cell's four
-// corner nodes.  Lanes with the same cell in consecutive lanes form a segment
-// (an ordered or cold plasma); a segmented suffix sum gives the segment's
-// first lane the segment's four totals, and only that lane adds them to the
-// shared mesh.  When no lane shares its cell with the lane before (a
-// disordered plasma) the shuffles are skipped.  key < 0: an empty slot.  All
-// 32 lanes must call this.
-// ---------------------------------------------------------------------------
-template <typename T>
-__device__ __forceinline__ void warp_deposit4(int key, T w0, T w1, T w2, T w3, T *mesh, int nx, int ny,
-                                              int lognx) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
-    const int prev = __shfl_up_sync(full, key, 1);
-    const bool head = (lane == 0) || (prev != key);
-    const unsigned heads = __ballot_sync(full, head);
-    if (heads != full) {
-        const unsigned above = (lane == 31) ? 0u : (heads & (0xffffffffu << (lane + 1)));
-        const int seg_end = above ? (__ffs(above) - 2) : 31;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const T b0 = __shfl_down_sync(full, w0, off), b1 = __shfl_down_sync(full, w1, off);
-            const T b2 = __shfl_down_sync(full, w2, off), b3 = __shfl_down_sync(full, w3, off);
-            if (lane + off <= seg_end) { w0 += b0; w1 += b1; w2 += b2; w3 += b3; }
-        }
-    }
-    if (head && key >= 0) {
-        const int di = key & (nx - 1), dj = key >> lognx, rs = nx + 1;      // padded rows
-        const int di1 = (di + 1) & (nx - 1), dj1 = (dj + 1) & (ny - 1);
-        atomicAdd(mesh + dj * rs + di, w0);
-        atomicAdd(mesh + dj * rs + di1, w1);
-        atomicAdd(mesh + dj1 * rs + di, w2);
-        atomicAdd(mesh + dj1 * rs + di1, w3);
-    }
-}
-
-// ---------------------------------------------------------------------------
 // The fused particle pass
 // ---------------------------------------------------------------------------
 template <typename T> struct Part { T x, y, vx, vy, w, sx, sy, rx, ry; };
@@ -364,8 +327,7 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
         if (DEC) { c.sx = qx[p]; c.sy = qy[p]; c.rx = px[p]; c.ry = py[p]; }
         else { c.sx = c.sy = c.rx = c.ry = T(0); }
     };
-    // the trip count is warp-uniform (the deposit is a warp operation); lanes
-    // past the end carry empty deposit slots
+    // lanes past the end of the particles carry empty deposit slots
     const int lognx = __ffs(nx) - 1;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -444,7 +406,18 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
             (void)di1; (void)dj1;
         }
         }
-        if (DEP) warp_deposit4<T>(dkey, d0, d1, d2, d3, mesh, nx, ny, lognx);
+        if (DEP && dkey >= 0) {
+            // one shared atomic per corner: the lattice start puts a warp's
+            // lanes in neighbouring cells of a row, and a disordered plasma
+            // spreads them, so aggregating lanes of one cell (which costs
+            // shuffles on every particle) does not pay here
+            const int di = dkey & (nx - 1), dj = dkey >> lognx;
+            const int di1 = (di + 1) & (nx - 1), dj1 = (dj + 1) & (ny - 1);
+            atomicAdd(mesh + dj * rs + di, d0);
+            atomicAdd(mesh + dj * rs + di1, d1);
+            atomicAdd(mesh + dj1 * rs + di, d2);
+            atomicAdd(mesh + dj1 * rs + di1, d3);
+        }
     }
     __syncthreads();
     if (DEP) {
