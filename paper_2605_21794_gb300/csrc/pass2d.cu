@@ -604,20 +604,38 @@ __global__ void __launch_bounds__(256) k_init_lattice2d(swpic2d_lattice f, doubl
     const double uc = f.vmin + (k + 0.5) * dvx, wc = f.vmin + (l + 0.5) * dvy;
     double sx = 0.0, sy = 0.0, tx = 0.0, ty = 0.0;
     if (f.decorate) {
+        // f0 factors: (1 + alpha (cos kx x cos ky y - sin kx x sin ky y)) e(vx) e(vy) / (2 pi vth^2),
+        // and each moment weight depends on one coordinate, so the n^4 rule is a
+        // sum over (x, y) nodes times sums over the vx and vy nodes: the
+        // transcendentals are taken per axis node, not per 4D node
         const int nq = f.quad_order;
+        const double iv = 1.0 / (2.0 * f.vth * f.vth);
+        double cxr[4], sxr[4], cys[4], sys_[4], pxr[4], pys[4];
+        double bx = 0.0, by = 0.0, bqx = 0.0, bqy = 0.0;
+        for (int r = 0; r < nq; ++r) {
+            const double x = xc + 0.5 * dx * gl[r], y = yc + 0.5 * dy * gl[r];
+            cxr[r] = cos(f.kx * x); sxr[r] = sin(f.kx * x);
+            cys[r] = cos(f.ky * y); sys_[r] = sin(f.ky * y);
+            pxr[r] = (Lx / (2.0 * M_PI)) * sin(2.0 * M_PI * (xc - x) / Lx);
+            pys[r] = (Ly / (2.0 * M_PI)) * sin(2.0 * M_PI * (yc - y) / Ly);
+            const double vx = uc + 0.5 * dvx * gl[r], vy = wc + 0.5 * dvy * gl[r];
+            const double ex = gl[8 + r] * exp(-vx * vx * iv), ey = gl[8 + r] * exp(-vy * vy * iv);
+            bx += ex; bqx += -ex * (uc - vx);
+            by += ey; bqy += -ey * (wc - vy);
+        }
+        double a0 = 0.0, ax = 0.0, ay = 0.0;
         for (int r = 0; r < nq; ++r)
-            for (int s = 0; s < nq; ++s)
-                for (int t = 0; t < nq; ++t)
-                    for (int u = 0; u < nq; ++u) {
-                        const double x = xc + 0.5 * dx * gl[r], y = yc + 0.5 * dy * gl[s];
-                        const double vx = uc + 0.5 * dvx * gl[t], vy = wc + 0.5 * dvy * gl[u];
-                        const double wgt = gl[8 + r] * gl[8 + s] * gl[8 + t] * gl[8 + u] * 0.0625 * dx * dy * dvx * dvy;
-                        const double fv = wgt * f0_lattice(f, x, y, vx, vy);
-                        sx += fv * (Lx / (2.0 * M_PI)) * sin(2.0 * M_PI * (xc - x) / Lx);
-                        sy += fv * (Ly / (2.0 * M_PI)) * sin(2.0 * M_PI * (yc - y) / Ly);
-                        tx += -fv * (uc - vx);
-                        ty += -fv * (wc - vy);
-                    }
+            for (int s = 0; s < nq; ++s) {
+                const double F = gl[8 + r] * gl[8 + s] * (1.0 + f.alpha * (cxr[r] * cys[s] - sxr[r] * sys_[s]));
+                a0 += F;
+                ax += F * pxr[r];
+                ay += F * pys[s];
+            }
+        const double K = 0.0625 * dx * dy * dvx * dvy / (2.0 * M_PI * f.vth * f.vth);
+        sx = K * ax * bx * by;
+        sy = K * ay * bx * by;
+        tx = K * a0 * bqx * by;
+        ty = K * a0 * bx * bqy;
     }
     static_cast<T *>(a.Qx)[p] = (T)xc;
     static_cast<T *>(a.Qy)[p] = (T)yc;

@@ -285,3 +285,16 @@ def test_oblique_landau_damping_rate():
     root = ph.landau_root(0.5, 1.4 - 0.15j)
     g, _, _ = ph.rate_fit(d[:, 0], d[:, 7], 1.0, 8.0, min_sep=1.0)
     assert g == pytest.approx(root.imag, rel=0.10), (g, root)
+
+
+def test_largest_fp64_mesh_one_step():
+    """The largest FP64 mesh (64 x 64 = 4096 nodes; table and padded mesh fill
+    166 KB of shared memory): one decorated FP64 step against the oracle."""
+    need_gpu()
+    Lx, Ly, nx, ny, dt = 4 * np.pi, 4 * np.pi, 64, 64, 0.05
+    st = W.random_state_2d(20000, Lx, Ly, seed=18, nx=nx, ny=ny, alpha=0.2)
+    got, diag, _ = _run(64, st, Lx, Ly, nx, ny, dt, 1, diag_every=1)
+    ref = O.run2d(st, nx, ny, Lx, Ly, dt, 1, diag_every=1)
+    _compare(got, ref, Lx, Ly, 1e-12)
+    for c in range(1, 8):
+        assert rel_max(diag[:, c], ref["diag"][:, c]) < 1e-11, c
