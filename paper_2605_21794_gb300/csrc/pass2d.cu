@@ -6,7 +6,10 @@
 //                 closing half-kick, diagnostics at the integer time, opening
 //                 half-kick, drift, wrap, deposit of the drifted monopole +
 //                 dipole charge into a per-CTA shared mesh, flush to a global
-//                 64-bit fixed-point accumulator (Eq. swpic_poisson, S_h = delta)
+//                 64-bit fixed-point accumulator (Eq. swpic_poisson, S_h = delta);
+//                 in FP32 contexts its last CTA writes the diagnostic record and
+//                 solves the new field in FP32 (solve_tail_f32)
+//   FP64 contexts solve in four kernels:
 //   k_rows_fwd    node loads -> FP64, forward DFT of every mesh row
 //   k_cols        per column: forward DFT, divide by the Q1 stiffness symbol
 //                 (zero mode dropped: neutralising background + zero-mean gauge),
@@ -14,9 +17,11 @@
 //   k_rows_inv    inverse DFT of every row -> Phi, field energy (1/2) Phi^T b
 //   k_table       lumped projection g of grad phi_h, node table (Phi, g) in the
 //                 state precision
-//   k_record      one diagnostic record
+//   k_record      one diagnostic record (FP64 contexts)
+//   k_init_lattice2d  the lattice start
 //
-// The DFTs are radix-2 in shared memory, one CTA per row or column, in FP64.
+// The DFTs are radix-2 in shared memory: one CTA per row or column in FP64,
+// the whole mesh in one CTA in FP32.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -395,7 +400,6 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
             // psi* N_c(Q) - p* . grad N_c(Q) for the four corners
             T u, v;
             const int di = cell_of(x, ihx, cmx, u), dj = cell_of(y, ihy, cmy, v);
-            const int di1 = (di + 1 == nx) ? 0 : di + 1, dj1 = (dj + 1 == ny) ? 0 : dj + 1;
             const T ou = T(1) - u, ov = T(1) - v;
             const T ax = DEC ? rx * ihx : T(0), ay = DEC ? ry * ihy : T(0);
             dkey = (dj << lognx) + di;
@@ -403,7 +407,6 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
             d1 = w * u * ov - ax * ov + ay * u;
             d2 = w * ou * v + ax * v - ay * ou;
             d3 = w * u * v - ax * v - ay * u;
-            (void)di1; (void)dj1;
         }
         }
         if (DEP && dkey >= 0) {
