@@ -298,3 +298,31 @@ def test_largest_fp64_mesh_one_step():
     _compare(got, ref, Lx, Ly, 1e-12)
     for c in range(1, 8):
         assert rel_max(diag[:, c], ref["diag"][:, c]) < 1e-11, c
+
+
+@pytest.mark.parametrize("precision", [32, 64])
+def test_accumulator_overflow_is_reported_and_a_refresh_recovers(precision):
+    """Weights scaled far beyond the fixed-point unit taken at refresh: the
+    deposit flags the overflow (no wrap-around), the next synchronous call
+    reports SWPIC_ENUMERIC, and a refresh takes a new unit."""
+    need_gpu()
+    import torch
+    from paper_2605_21794_gb300 import swpic
+    L, nx = 4.0, 16
+    st = W.random_state_2d(1000, L, L, seed=19, nx=nx, ny=nx)
+    sim = _sim(L, L, nx, nx, 0.05, 1000, precision)
+    try:
+        sim.init_particles(st)
+        torch.cuda.synchronize()
+        sim.t["psi"].mul_(1e6)
+        torch.cuda.synchronize()
+        sim.step(1)
+        with pytest.raises(swpic.SwpicError) as e:
+            swpic.swpic2d_synchronize(sim.ctx)
+        assert e.value.status == swpic.SWPIC_ENUMERIC
+        swpic.swpic2d_refresh(sim.ctx)
+        sim.step(2, 1)
+        d = sim.diagnostics()
+        assert np.all(np.isfinite(d[-3:, 1:8]))
+    finally:
+        sim.close()
