@@ -132,6 +132,17 @@ swpic_status swpic2d_get_field(swpic2d_ctx *ctx, double *b, double *Phi, double 
 /* Synchronous: wait for the stream; report a device anomaly flag. */
 swpic_status swpic2d_synchronize(swpic2d_ctx *ctx);
 
+/* Checkpoint (synchronous).  swpic2d_save writes the bound state (the nine
+ * arrays, or five without decorations, in the context's precision), the step
+ * count and the geometry to a binary file; SWPIC_EIO when it cannot be
+ * written.  swpic2d_load reads such a file into the bound arrays of a
+ * context with the same precision, decoration flag, particle count, mesh,
+ * domain and dt (SWPIC_EINVAL otherwise, SWPIC_EIO when unreadable),
+ * restores the step count and takes the field of the state (as
+ * swpic2d_refresh).  Diagnostic records stay in the context that made them. */
+swpic_status swpic2d_save(swpic2d_ctx *ctx, const char *path);
+swpic_status swpic2d_load(swpic2d_ctx *ctx, const char *path);
+
 /* Per-pass device durations (CUDA events around every particle pass of
  * swpic2d_step while enabled; read and cleared by swpic2d_pass_times). */
 swpic_status swpic2d_set_timing(swpic2d_ctx *ctx, int32_t enable);

@@ -458,6 +458,77 @@ swpic_status swpic2d_get_field(swpic2d_ctx *ctx, double *b, double *Phi, double 
     return check_flag(ctx);
 }
 
+// ---- checkpoint ----------------------------------------------------------
+static const char kMagic2d[8] = {'S', 'W', 'P', '2', 'D', 'v', '1', 0};
+
+struct Header2d {
+    int32_t prec, dec, nx, ny;
+    int64_t n, step, last_rec;
+    double Lx, Ly, dt;
+};
+
+swpic_status swpic2d_save(swpic2d_ctx *ctx, const char *path) {
+    if (!ctx || !path) return SWPIC_EINVAL;
+    if (!ctx->bound) return fail(ctx, SWPIC_ESTATE, "no state bound");
+    CK2(cudaStreamSynchronize(ctx->stream));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, SWPIC_EIO, std::string("cannot open ") + path);
+    const Header2d h{ctx->prec, ctx->dec ? 1 : 0, ctx->cfg.nx, ctx->cfg.ny, ctx->n, ctx->step, ctx->last_rec,
+                     ctx->cfg.Lx, ctx->cfg.Ly, ctx->cfg.dt};
+    bool ok = std::fwrite(kMagic2d, 1, 8, f) == 8 && std::fwrite(&h, sizeof(h), 1, f) == 1;
+    const size_t bytes = (size_t)ctx->n * (ctx->prec == SWPIC_F64 ? 8 : 4);
+    std::vector<unsigned char> buf(bytes);
+    for (int k = 0; k < 9 && ok; ++k) {
+        if (!ctx->st[k] || bytes == 0) continue;
+        const cudaError_t e = cudaMemcpy(buf.data(), ctx->st[k], bytes, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return fail(ctx, SWPIC_ECUDA, std::string("save: ") + cudaGetErrorString(e));
+        }
+        ok = std::fwrite(buf.data(), 1, bytes, f) == bytes;
+    }
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? SWPIC_OK : fail(ctx, SWPIC_EIO, std::string("cannot write ") + path);
+}
+
+swpic_status swpic2d_load(swpic2d_ctx *ctx, const char *path) {
+    if (!ctx || !path) return SWPIC_EINVAL;
+    if (!ctx->bound) return fail(ctx, SWPIC_ESTATE, "no state bound");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, SWPIC_EIO, std::string("cannot open ") + path);
+    char magic[8];
+    Header2d h{};
+    if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMagic2d, 8) != 0 ||
+        std::fread(&h, sizeof(h), 1, f) != 1) {
+        std::fclose(f);
+        return fail(ctx, SWPIC_EIO, std::string("not a 2D checkpoint: ") + path);
+    }
+    if (h.prec != ctx->prec || h.dec != (ctx->dec ? 1 : 0) || h.nx != ctx->cfg.nx || h.ny != ctx->cfg.ny ||
+        h.n != ctx->n || h.Lx != ctx->cfg.Lx || h.Ly != ctx->cfg.Ly || h.dt != ctx->cfg.dt) {
+        std::fclose(f);
+        return fail(ctx, SWPIC_EINVAL, "checkpoint does not match this context");
+    }
+    CK2(cudaStreamSynchronize(ctx->stream));
+    const size_t bytes = (size_t)ctx->n * (ctx->prec == SWPIC_F64 ? 8 : 4);
+    std::vector<unsigned char> buf(bytes);
+    for (int k = 0; k < 9; ++k) {
+        if (!ctx->st[k] || bytes == 0) continue;
+        if (std::fread(buf.data(), 1, bytes, f) != bytes) {
+            std::fclose(f);
+            return fail(ctx, SWPIC_EIO, std::string("truncated checkpoint: ") + path);
+        }
+        const cudaError_t e = cudaMemcpy(ctx->st[k], buf.data(), bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            std::fclose(f);
+            return fail(ctx, SWPIC_ECUDA, std::string("load: ") + cudaGetErrorString(e));
+        }
+    }
+    std::fclose(f);
+    ctx->step = h.step;
+    ctx->last_rec = h.last_rec;
+    return swpic2d_refresh(ctx);
+}
+
 swpic_status swpic2d_synchronize(swpic2d_ctx *ctx) {
     if (!ctx) return SWPIC_EINVAL;
     CK2(cudaStreamSynchronize(ctx->stream));

@@ -125,6 +125,8 @@ SIGNATURES = {
     "swpic2d_diagnostics": (C.c_int, [_CTX, C.POINTER(swpic2d_diag), C.c_int32, C.POINTER(C.c_int32)]),
     "swpic2d_get_field": (C.c_int, [_CTX, _D, _D, _D, _D]),
     "swpic2d_synchronize": (C.c_int, [_CTX]),
+    "swpic2d_save": (C.c_int, [_CTX, C.c_char_p]),
+    "swpic2d_load": (C.c_int, [_CTX, C.c_char_p]),
     "swpic2d_set_timing": (C.c_int, [_CTX, C.c_int32]),
     "swpic2d_pass_times": (C.c_int, [_CTX, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
     "swpic2d_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
@@ -524,6 +526,14 @@ def swpic2d_get_field(ctx, nx, ny):
 
 def swpic2d_synchronize(ctx):
     _check2(load_library().swpic2d_synchronize(ctx), ctx)
+
+
+def swpic2d_save(ctx, path):
+    _check2(load_library().swpic2d_save(ctx, path.encode()), ctx)
+
+
+def swpic2d_load(ctx, path):
+    _check2(load_library().swpic2d_load(ctx, path.encode()), ctx)
 
 
 def swpic2d_set_timing(ctx, enable):

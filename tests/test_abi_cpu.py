@@ -144,6 +144,8 @@ def test_2d_create_rejects_bad_configs_before_touching_the_device(lib):
         assert lib.swpic2d_create(C.byref(c), 10, C.byref(ctx)) == swpic.SWPIC_EINVAL
     assert lib.swpic2d_create(C.byref(cfg()), -1, C.byref(ctx)) == swpic.SWPIC_EINVAL
     assert lib.swpic2d_step(None, 1, 0) == swpic.SWPIC_EINVAL
+    assert lib.swpic2d_save(None, b"x") == swpic.SWPIC_EINVAL
+    assert lib.swpic2d_load(None, b"x") == swpic.SWPIC_EINVAL
     assert lib.swpic2d_refresh(None) == swpic.SWPIC_EINVAL
     lib.swpic2d_destroy(None)
 

@@ -326,3 +326,44 @@ def test_accumulator_overflow_is_reported_and_a_refresh_recovers(precision):
         assert np.all(np.isfinite(d[-3:, 1:8]))
     finally:
         sim.close()
+
+
+def test_checkpoint_resume(tmp_path):
+    """Save after 3 FP64 steps, run 4 more; a fresh context loading the file
+    and running the same 4 steps reaches the same state (up to the order of
+    the deposit's shared-memory sums) with the same step numbering; a
+    mismatched context and a missing file are refused."""
+    need_gpu()
+    from paper_2605_21794_gb300 import swpic
+    Lx, Ly, nx, ny, dt = 5.0, 4.0, 16, 16, 0.05
+    st = W.random_state_2d(2500, Lx, Ly, seed=20, nx=nx, ny=ny, alpha=0.2)
+    path = str(tmp_path / "ck.bin")
+    a = _sim(Lx, Ly, nx, ny, dt, 2500, 64)
+    try:
+        a.init_particles(st)
+        a.step(3, 1)
+        swpic.swpic2d_save(a.ctx, path)
+        a.step(4, 1)
+        ref, dref = a.state(), a.diagnostics()
+    finally:
+        a.close()
+    b = _sim(Lx, Ly, nx, ny, dt, 2500, 64)
+    try:
+        swpic.swpic2d_load(b.ctx, path)
+        b.step(4, 1)
+        got, dgot = b.state(), b.diagnostics()
+    finally:
+        b.close()
+    _compare(got, ref, Lx, Ly, 1e-12)
+    np.testing.assert_array_equal(dgot[:, 8], np.arange(4, 8))
+    assert rel_max(dgot[:, 6], dref[-4:, 6]) < 1e-12
+    c = _sim(Lx, Ly, nx, ny, dt, 2500, 32)
+    try:
+        with pytest.raises(swpic.SwpicError) as e:
+            swpic.swpic2d_load(c.ctx, path)
+        assert e.value.status == swpic.SWPIC_EINVAL
+        with pytest.raises(swpic.SwpicError) as e:
+            swpic.swpic2d_load(c.ctx, str(tmp_path / "missing.bin"))
+        assert e.value.status == swpic.SWPIC_EIO
+    finally:
+        c.close()
