@@ -118,6 +118,15 @@ swpic_status swpic2d_init_lattice(swpic2d_ctx *ctx, const swpic2d_lattice *spec)
  * s, including the starting time). */
 swpic_status swpic2d_step(swpic2d_ctx *ctx, int32_t n_steps, int32_t diag_every);
 
+/* Synchronous.  The whole path from host memory: copy the nine host arrays
+ * in[9] (Qx, Qy, Px, Py, qx, qy, px, py, psi in the context's precision;
+ * a NULL decoration array is taken as zero) into the bound device state,
+ * take its field (as swpic2d_refresh), advance n_steps, and copy the eight
+ * evolving arrays back into out[8] (NULL entries are skipped).  Pinned host
+ * memory makes the copies asynchronous. */
+swpic_status swpic2d_step_host(swpic2d_ctx *ctx, const void *const in[9], void *const out[8],
+                               int32_t n_steps, int32_t diag_every);
+
 /* Synchronous: copy up to max_records records into out (host). */
 swpic_status swpic2d_diagnostics(swpic2d_ctx *ctx, swpic2d_diag *out, int32_t max_records,
                                  int32_t *n_records);

@@ -458,6 +458,28 @@ swpic_status swpic2d_get_field(swpic2d_ctx *ctx, double *b, double *Phi, double 
     return check_flag(ctx);
 }
 
+swpic_status swpic2d_step_host(swpic2d_ctx *ctx, const void *const in[9], void *const out[8],
+                               int32_t n_steps, int32_t diag_every) {
+    if (!ctx || !in || n_steps < 0 || diag_every < 0) return SWPIC_EINVAL;
+    if (!ctx->bound) return fail(ctx, SWPIC_ESTATE, "no state bound");
+    const size_t bytes = (size_t)ctx->n * (ctx->prec == SWPIC_F64 ? 8 : 4);
+    for (int k = 0; k < 9; ++k) {
+        if (!ctx->st[k] || bytes == 0) continue;
+        if (in[k]) CK2(cudaMemcpyAsync(ctx->st[k], in[k], bytes, cudaMemcpyHostToDevice, ctx->stream));
+        else if (k >= 4 && k <= 7) CK2(cudaMemsetAsync(ctx->st[k], 0, bytes, ctx->stream));
+        else return fail(ctx, SWPIC_EINVAL, "missing host array");
+    }
+    swpic_status s = swpic2d_refresh(ctx);
+    if (s != SWPIC_OK) return s;
+    s = swpic2d_step(ctx, n_steps, diag_every);
+    if (s != SWPIC_OK) return s;
+    if (out)
+        for (int k = 0; k < 8; ++k)
+            if (out[k] && ctx->st[k] && bytes)
+                CK2(cudaMemcpyAsync(out[k], ctx->st[k], bytes, cudaMemcpyDeviceToHost, ctx->stream));
+    return swpic2d_synchronize(ctx);
+}
+
 // ---- checkpoint ----------------------------------------------------------
 static const char kMagic2d[8] = {'S', 'W', 'P', '2', 'D', 'v', '1', 0};
 

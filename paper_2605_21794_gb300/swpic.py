@@ -125,6 +125,7 @@ SIGNATURES = {
     "swpic2d_diagnostics": (C.c_int, [_CTX, C.POINTER(swpic2d_diag), C.c_int32, C.POINTER(C.c_int32)]),
     "swpic2d_get_field": (C.c_int, [_CTX, _D, _D, _D, _D]),
     "swpic2d_synchronize": (C.c_int, [_CTX]),
+    "swpic2d_step_host": (C.c_int, [_CTX, C.POINTER(_P), C.POINTER(_P), C.c_int32, C.c_int32]),
     "swpic2d_save": (C.c_int, [_CTX, C.c_char_p]),
     "swpic2d_load": (C.c_int, [_CTX, C.c_char_p]),
     "swpic2d_set_timing": (C.c_int, [_CTX, C.c_int32]),
@@ -526,6 +527,13 @@ def swpic2d_get_field(ctx, nx, ny):
 
 def swpic2d_synchronize(ctx):
     _check2(load_library().swpic2d_synchronize(ctx), ctx)
+
+
+def swpic2d_step_host(ctx, in_ptrs, out_ptrs, n_steps, diag_every=0):
+    """Host pointers: in_ptrs[9] (STATE2D order), out_ptrs[8] (None entries skipped)."""
+    a = (_P * 9)(*[None if p is None else int(p) for p in in_ptrs])
+    b = (_P * 8)(*[None if p is None else int(p) for p in out_ptrs])
+    _check2(load_library().swpic2d_step_host(ctx, a, b, int(n_steps), int(diag_every)), ctx)
 
 
 def swpic2d_save(ctx, path):

@@ -367,3 +367,23 @@ def test_checkpoint_resume(tmp_path):
         assert e.value.status == swpic.SWPIC_EIO
     finally:
         c.close()
+
+
+def test_host_entry_point_equals_device_path():
+    """swpic2d_step_host from host arrays (copies, refresh, steps, copies
+    back) reaches the device path's state (FP64, up to the order of the
+    deposit's shared-memory sums)."""
+    need_gpu()
+    from paper_2605_21794_gb300 import swpic
+    Lx, Ly, nx, ny, dt = 5.0, 4.0, 16, 16, 0.05
+    st = W.random_state_2d(2100, Lx, Ly, seed=21, nx=nx, ny=ny, alpha=0.2)
+    ref, _, _ = _run(64, st, Lx, Ly, nx, ny, dt, 5, diag_every=0)
+    sim = _sim(Lx, Ly, nx, ny, dt, 2100, 64)
+    try:
+        hin = [np.ascontiguousarray(st[k], dtype=np.float64) for k in swpic.STATE2D]
+        hout = [np.zeros(2100) for _ in swpic.STATE2D[:8]]
+        swpic.swpic2d_step_host(sim.ctx, [a.ctypes.data for a in hin], [a.ctypes.data for a in hout], 5, 0)
+    finally:
+        sim.close()
+    got = dict(zip(swpic.STATE2D[:8], hout))
+    _compare(got, ref, Lx, Ly, 1e-12)
