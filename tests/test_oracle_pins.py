@@ -213,6 +213,55 @@ def test_d2_lumped_exact_for_quadratic_interior():
     assert np.allclose(d2[1:nx - 2], 6.0, atol=1e-10)
 
 
+def test_d2_nodal_converges_second_order_to_phi_second_derivative():
+    """NODAL (reading A1): the nodal phi'' is the lumped projection -btilde/h of
+    the distributional phi_h'' of the P1 field.  For Phi_j = cos(q_j) and the
+    charge that produces it, btilde = A Phi (the stiffness matrix), the nodal
+    values converge at second order to phi'' = -cos at the nodes."""
+    L = 2 * np.pi
+    errs = []
+    for nx in (32, 64, 128):
+        h = L / nx
+        q = np.arange(nx) * h
+        Phi = np.cos(q)
+        bt = O.stiffness(nx, L) @ Phi
+        _, d2 = O.field_tables(Phi, L, O.D2_NODAL, btilde=bt)
+        errs.append(np.abs(d2 + np.cos(q)).max())
+    assert errs[2] < 1e-3
+    assert 3.5 < errs[0] / errs[1] < 4.5 and 3.5 < errs[1] / errs[2] < 4.5
+
+
+def test_nodal_gather_is_periodic_linear_interpolation():
+    """The nodal branch of the gather interpolates the nodal phi'' linearly
+    inside each element, periodically across x = L (checked against numpy's
+    periodic interpolation), and reads phi_h' as the element slope."""
+    L, nx = 7.0, 11
+    h = L / nx
+    s = W.uniform01(21, 0, nx) - 0.5
+    dphi = W.uniform01(21, 1, nx)
+    Q = np.concatenate([W.uniform01(21, 2, 400) * L, np.arange(nx) * h, [L - 1e-12]])
+    dV, d2V = O.gather(Q, L, dphi, s, d2_mode=O.D2_NODAL)
+    ref = np.interp(Q, np.arange(nx) * h, s, period=L)
+    assert np.abs(d2V - ref).max() < 1e-12
+    assert np.array_equal(dV, dphi[O.element(Q, L, nx)])
+
+
+def test_nodal_gather_of_a_smooth_field_is_second_order_at_particles():
+    """Whole NODAL chain at arbitrary particle positions: Phi = cos sampled on
+    the nodes, btilde = A Phi, table, gather -> phi''(Q) = -cos Q + O(h^2)."""
+    L = 2 * np.pi
+    Q = W.uniform01(5, 0, 1000) * L
+    errs = []
+    for nx in (32, 64, 128):
+        h = L / nx
+        Phi = np.cos(np.arange(nx) * h)
+        bt = O.stiffness(nx, L) @ Phi
+        dphi, d2 = O.field_tables(Phi, L, O.D2_NODAL, btilde=bt)
+        _, d2V = O.gather(Q, L, dphi, d2, d2_mode=O.D2_NODAL)
+        errs.append(np.abs(d2V + np.cos(Q)).max())
+    assert 3.3 < errs[0] / errs[1] < 4.7 and 3.3 < errs[1] / errs[2] < 4.7
+
+
 def test_d2_nodal_is_minus_neutral_charge_density():
     L, nx = 4.0, 8
     h = L / nx
@@ -468,6 +517,33 @@ def test_two_stream_growth_rate():
     sel = (t >= 10.0) & (t <= 30.0)
     g = np.polyfit(t[sel], np.log(E[sel]), 1)[0]
     assert abs(g / root.imag - 1) < 0.01
+
+
+def test_strong_landau_paper_setup_damping_rate():
+    """Sec. 7.3 (strong Landau damping): L = 12, A = 0.5, k = 2 pi/L, a 100-element
+    CG mesh, dt = 0.2.  The paper prints gamma = -0.236 for its E_amp history
+    (fit method not stated, reading A10).  With the lattice start (reading A6)
+    on 128^2 and 256^2 lattices, the least-squares fit of log E_amp over the
+    maxima in t in [0, 15] is within 7% of the printed rate for the decorated
+    run (reading A1, LUMPED) and the decorated and point-particle runs agree
+    to 1%; the 7% covers the maxima that enter or leave the window as the
+    lattice changes (fits of -0.224 ... -0.251 between 128^2 and 256^2).  The
+    decorated run stays finite over the fitted time (the decorations' growth
+    at later times is described with the findings of the oracle)."""
+    L = 12.0
+    for side in (128, 256):
+        lat = W.LatticeSpec(side, side, L, -6.0, 6.0, 0.5, 2 * math.pi / L, W.MAXWELL)
+        st = O.init_lattice(lat)
+        rates = []
+        for dec in (True, False):
+            r = O.run(st, 100, L, 0.2, 250, diag_every=1, decorated=dec)
+            t, E = r["diag"][:, 0], r["diag"][:, 6]
+            assert np.all(np.isfinite(E))
+            g, _, peaks = ph.rate_fit(t, E, 0.0, 15.0, min_sep=1.0)
+            assert len(peaks) >= 5
+            rates.append(g)
+        assert abs(rates[0] / -0.236 - 1) < 0.07, (side, rates)
+        assert abs(rates[0] / rates[1] - 1) < 0.01, (side, rates)
 
 
 def test_wrap_maps_round_up_into_domain():
