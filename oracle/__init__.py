@@ -62,6 +62,8 @@ def lib():
                                         C.c_int32, C.c_int32, _D, _D, _D, _D, _D]
         L.or_gauss_legendre.restype = C.c_int
         L.or_gauss_legendre.argtypes = [C.c_int32, _D, _D]
+        L.or_set_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
         L.or_init_lattice.restype = C.c_int
         L.or_kmeans_assign.argtypes = [C.c_int64, _D, _D, C.c_int32, _D, _D, C.c_double, _I32]
         L.or_kmeans_assign.restype = None
@@ -256,6 +258,14 @@ def field_of_state(Q, p_star, psi_star, L, nx, d2_mode=D2_LUMPED, decorated=True
     if rc != 0:
         raise RuntimeError("oracle field_of_state failed")
     return out
+
+
+def set_threads(n):
+    """Host threads of or_run's particle loops (1 = the serial loops every
+    test uses; more splits the particles into blocks whose deposit and
+    diagnostic partials are added in block order).  Returns the count in
+    effect (1 when the oracle was built without OpenMP)."""
+    return int(lib().or_set_threads(int(n)))
 
 
 def run(state, nx, L, dt, n_steps, diag_every=1, d2_mode=D2_LUMPED, decorated=True,

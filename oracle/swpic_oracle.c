@@ -38,6 +38,28 @@ static void nsum_add(nsum *acc, double x) {
 }
 static double nsum_val(const nsum *acc) { return acc->s + acc->c; }
 
+/* Host threads for the particle loops of or_run (default 1: the plain serial
+ * loops that every test uses).  With T > 1 (an OpenMP build) the particles
+ * are split into T contiguous blocks: gather, kick and drift act particle by
+ * particle (same results), while the deposit and the particle sums of the
+ * diagnostics give one partial per block, added in block order, so the
+ * results depend on T only through that summation order.  This exists to
+ * time the oracle on all host cores; it changes none of its arithmetic. */
+static int g_threads = 1;
+int or_set_threads(int t) {
+#ifdef _OPENMP
+    g_threads = t < 1 ? 1 : t;
+#else
+    (void)t;
+    g_threads = 1;
+#endif
+    return g_threads;
+}
+static void block_of(int64_t n, int T, int t, int64_t *a0, int64_t *a1) {
+    *a0 = n * t / T;
+    *a1 = n * (t + 1) / T;
+}
+
 /* Periodic wrap of a position into [0, L) (torus T = R mod L, Sec. 2).
  * A value that rounds up to exactly L is mapped to L - L = 0 (reading A5). */
 double or_wrap(double Q, double L) {
@@ -362,15 +384,41 @@ void or_drift(int64_t n, double *Q, const double *P, const double *q_star,
 /*  E_amp     = ( (1/L) int_0^L E^2 dq )^{1/2}   (Eq. Eamp), E = -phi_h'     */
 /* out = {mass, momentum, kinetic, field, H, E_amp}                          */
 /* ------------------------------------------------------------------------ */
-void or_diagnostics(int64_t n, const double *P, const double *q_star,
-                    const double *psi_star, int32_t nx, double L,
-                    const double *Phi, double *out) {
+static void particle_sums(int64_t a0, int64_t a1, const double *P, const double *q_star,
+                          const double *psi_star, nsum out[3]) {
     nsum mass = {0, 0}, mom = {0, 0}, kin = {0, 0};
-    for (int64_t a = 0; a < n; ++a) {
+    for (int64_t a = a0; a < a1; ++a) {
         double qs = q_star ? q_star[a] : 0.0;
         nsum_add(&mass, psi_star[a]);
         nsum_add(&mom, psi_star[a] * P[a] + qs);
         nsum_add(&kin, 0.5 * psi_star[a] * P[a] * P[a] + qs * P[a]);
+    }
+    out[0] = mass; out[1] = mom; out[2] = kin;
+}
+
+void or_diagnostics(int64_t n, const double *P, const double *q_star,
+                    const double *psi_star, int32_t nx, double L,
+                    const double *Phi, double *out) {
+    nsum mass = {0, 0}, mom = {0, 0}, kin = {0, 0};
+    if (g_threads <= 1) {
+        nsum r[3];
+        particle_sums(0, n, P, q_star, psi_star, r);
+        mass = r[0]; mom = r[1]; kin = r[2];
+    } else {
+        const int T = g_threads;
+        nsum *part = (nsum *)calloc((size_t)T * 3, sizeof(nsum));
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+        for (int t = 0; t < T; ++t) {
+            int64_t a0, a1;
+            block_of(n, T, t, &a0, &a1);
+            particle_sums(a0, a1, P, q_star, psi_star, part + 3 * t);
+        }
+        for (int t = 0; t < T; ++t) {       /* block order */
+            nsum_add(&mass, nsum_val(&part[3 * t]));
+            nsum_add(&mom, nsum_val(&part[3 * t + 1]));
+            nsum_add(&kin, nsum_val(&part[3 * t + 2]));
+        }
+        free(part);
     }
     double *A = (double *)malloc(sizeof(double) * (size_t)nx * nx);
     or_stiffness(nx, L, A);
@@ -442,8 +490,28 @@ static int field_update(or_field *f, int64_t n, const double *Q, const double *p
             for (int32_t j = 0; j < f->nx; ++j) { f->dphi[j] = to_f32(f->dphi[j]); f->d2[j] = to_f32(f->d2[j]); }
         return rc;
     }
-    or_deposit(n, Q, f->decorated ? p_star : NULL, psi_star, f->store_f32 ? f->elem : NULL,
-               f->L, f->nx, f->b);
+    if (g_threads <= 1 || f->store_f32) {
+        or_deposit(n, Q, f->decorated ? p_star : NULL, psi_star, f->store_f32 ? f->elem : NULL,
+                   f->L, f->nx, f->b);
+    } else {
+        /* one mesh per particle block, added in block order */
+        const int T = g_threads;
+        const int32_t nx = f->nx;
+        double *part = (double *)malloc(sizeof(double) * (size_t)T * nx);
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+        for (int t = 0; t < T; ++t) {
+            int64_t a0, a1;
+            block_of(n, T, t, &a0, &a1);
+            or_deposit(a1 - a0, Q + a0, (f->decorated && p_star) ? p_star + a0 : NULL, psi_star + a0, NULL,
+                       f->L, nx, part + (size_t)t * nx);
+        }
+        for (int32_t j = 0; j < nx; ++j) {
+            double v = 0.0;
+            for (int t = 0; t < T; ++t) v += part[(size_t)t * nx + j];
+            f->b[j] = v;
+        }
+        free(part);
+    }
     double lambda = 0.0;
     or_poisson_solve(f->solver, f->b, f->Phi, &lambda);
     for (int32_t j = 0; j < f->nx; ++j) f->btilde[j] = f->b[j] - lambda;
@@ -508,7 +576,33 @@ int or_run(int64_t n, double *Q, double *P, double *q_star, double *p_star,
     /* FP32 storage keeps the step coefficients in FP32 as well */
     const double half = store_f32 ? to_f32(0.5 * dt) : 0.5 * dt;
     const double full = store_f32 ? to_f32(dt) : dt;
+    /* threaded particle loops (see or_set_threads): P1 field, FP64 storage */
+    const int T = (g_threads > 1 && d2_mode != 3 && !store_f32) ? g_threads : 1;
     for (int32_t s = 1; rc == 0 && s <= n_steps; ++s) {
+        if (T > 1) {
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+            for (int t = 0; t < T; ++t) {
+                int64_t a0, a1;
+                block_of(n, T, t, &a0, &a1);
+                or_gather(a1 - a0, Q + a0, NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV + a0, f.d2V + a0);
+                or_kick_values(a1 - a0, ps ? ps + a0 : NULL, P + a0, qs ? qs + a0 : NULL, f.dV + a0,
+                               f.d2V + a0, half);
+                or_drift(a1 - a0, Q + a0, P + a0, qs ? qs + a0 : NULL, ps ? ps + a0 : NULL, L, full);
+            }
+            rc = field_update(&f, n, Q, ps, psi_star);
+            if (rc != 0) break;
+#pragma omp parallel for num_threads(T) schedule(static, 1)
+            for (int t = 0; t < T; ++t) {
+                int64_t a0, a1;
+                block_of(n, T, t, &a0, &a1);
+                or_gather(a1 - a0, Q + a0, NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV + a0, f.d2V + a0);
+                or_kick_values(a1 - a0, ps ? ps + a0 : NULL, P + a0, qs ? qs + a0 : NULL, f.dV + a0,
+                               f.d2V + a0, half);
+            }
+            if (diag && diag_every > 0 && s % diag_every == 0)
+                write_diag(diag + 7 * (nd++), (double)s * dt, n, P, qs, psi_star, &f);
+            continue;
+        }
         if (d2_mode == 3) or_p2_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, f.dV, f.d2V);
         else or_gather(n, Q, store_f32 ? f.elem : NULL, L, nx, f.dphi, f.d2, d2_mode, f.dV, f.d2V);
         or_kick_values(n, ps, P, qs, f.dV, f.d2V, half);
