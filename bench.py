@@ -176,38 +176,62 @@ def oracle_sample_spec(spec, cols):
     return dataclasses.replace(spec.lattice, nq=cols)
 
 
-def time_oracle(spec, cols, steps, warmup, diag_every, d2_mode=0):
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def time_oracle(spec, cols, steps, warmup, diag_every, d2_mode=0, threads=1):
+    """Seconds for `steps` oracle steps on a `cols`-column sample, per step
+    taken as [t(steps + 1) - t(1)] / steps: each oracle run factorises its
+    dense Poisson matrix once at set-up, and the difference leaves that
+    one-time cost out.  Returns (particles, seconds for `steps` steps,
+    threads used)."""
     import oracle as O
-    lat = oracle_sample_spec(spec, cols)
-    st = O.init_lattice(lat)
-    if warmup > 0:
-        st = O.run(st, spec.nx, lat.L, spec.dt, warmup, diag_every=diag_every, d2_mode=d2_mode)
-    t0 = time.perf_counter()
-    O.run(st, spec.nx, lat.L, spec.dt, steps, diag_every=diag_every, d2_mode=d2_mode)
-    dt = time.perf_counter() - t0
-    return lat.n, dt
+    used = O.set_threads(threads)
+    try:
+        lat = oracle_sample_spec(spec, cols)
+        st = O.init_lattice(lat)
+        if warmup > 0:
+            st = O.run(st, spec.nx, lat.L, spec.dt, warmup, diag_every=diag_every, d2_mode=d2_mode)
+        t0 = time.perf_counter()
+        O.run(st, spec.nx, lat.L, spec.dt, 1, diag_every=diag_every, d2_mode=d2_mode)
+        t1 = time.perf_counter()
+        O.run(st, spec.nx, lat.L, spec.dt, steps + 1, diag_every=diag_every, d2_mode=d2_mode)
+        t2 = time.perf_counter()
+    finally:
+        O.set_threads(1)
+    return lat.n, max((t2 - t1) - (t1 - t0), 1e-9), used
 
 
 def run_reference(args, spec):
     world, rank, _ = dist_env()
     if rank != 0:
         return
-    cols = max(1, min(spec.lattice.nq, 16))           # 16 x 4096 = 65,536 particles per step
+    cols = max(1, min(spec.lattice.nq, 256))          # 256 x 4096 = 1,048,576 particles per step
     d2 = D2_MODES[args.d2_mode]
     # the oracle's P2 field is a dense (2 nx + 1)^2 solve every step: a few steps only
     steps = min(args.steps, 5) if d2 == 3 else args.steps
     warm = min(args.warmup, 1) if d2 == 3 else args.warmup
-    n, dt = time_oracle(spec, cols, steps, warm, args.diag_every, d2)
+    n, dt, cores = time_oracle(spec, cols, steps, warm, args.diag_every, d2, threads=host_cores())
     value = n * steps / dt
+    sample = ("%d of %d lattice columns (%d particles) of %s, %d steps after %d warm-up steps, "
+              "plain-C FP64 oracle, particle loops on %d host threads; seconds per step = "
+              "[t(K+1 steps) - t(1 step)]/K (the one-time dense LU of each oracle run left out)" %
+              (cols, spec.lattice.nq, n, spec.name, steps, warm, cores))
+    config = dict(workload_config(spec, args, None),
+                  sample={"lattice_columns": cols, "particles": n, "steps": steps,
+                          "note": "each step of the oracle arm is one oracle step of this sample of "
+                                  "the workload; value = sample particles x steps / time"})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(spec, args, None),
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "%d of %d lattice columns (%d particles) of %s, %d steps, "
-                                       "single-threaded plain-C FP64 oracle" %
-                                       (cols, spec.lattice.nq, n, spec.name, steps)},
+            "config": config,
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -364,6 +388,8 @@ def main():
         if args.d2_mode != "p2":
             line["p2_elements"] = p2_leg(torch, swpic, spec, args, (tpb, bpsm, resort, stages), timed)
         line["two_d"] = two_d_leg(torch, swpic, args)
+        line["strong_landau"] = method_legs(torch, swpic, args, timed)
+        line["fp32_diag_error"] = fp32_diag_error_leg(torch, swpic, spec, args)
         line["cpu_baseline"] = cpu_baseline_leg(spec, args)
     elif rank == 0:
         restore(sim)
@@ -657,41 +683,219 @@ def ensemble_leg(torch, swpic):
                 raise
 
     def gamma_err(diags):
+        """Per run: the damping rate fitted over t in [2, t1], t1 = min(0.8 T_R,
+        2/|gamma_root|, 40) (at least 12): before the lattice recurrence T_R =
+        2 pi/(k dv), over about two e-folds of the damping, and before the
+        nonlinear trapping time of the larger alphas.  Median relative error
+        against the dispersion root over the runs with alpha < 0.05, by lattice
+        side, and over the resolved linear runs (side >= 256, alpha < 0.02)."""
         errs = []
         for r, d in zip(runs, diags):
-            if r.lattice.alpha >= 0.05:
+            lat = r.lattice
+            if lat.alpha >= 0.05:
                 continue
-            root = ph.landau_root(r.lattice.kx, 1.0 + 0.5 * r.lattice.kx - 0.1j)
+            root = ph.landau_root(lat.kx, 1.0 + 0.5 * lat.kx - 0.1j)
+            t_rec = 2 * np.pi / (lat.kx * (lat.vmax - lat.vmin) / lat.nv)
+            t1 = max(12.0, min(0.8 * t_rec, 2.0 / abs(root.imag), 40.0))
             try:
-                g, _, _ = ph.rate_fit(d[:, 0], d[:, 6], 2.0, 12.0, min_sep=1.2)
+                g, _, _ = ph.rate_fit(d[:, 0], d[:, 6], 2.0, t1, min_sep=1.2)
             except ValueError:
                 continue
-            errs.append(abs(g / root.imag - 1))
-        return float(np.median(errs)) if errs else None, len(errs)
+            errs.append((lat.nq, lat.alpha, abs(g / root.imag - 1)))
+        med = lambda xs: float(np.median(xs)) if xs else None
+        return {"median_alpha_lt_0.05": med([e for _, _, e in errs]), "runs_fitted": len(errs),
+                "median_by_side": {str(sd): med([e for s_, _, e in errs if s_ == sd]) for sd in (64, 128, 256, 512)},
+                "median_side_ge_256_alpha_lt_0.02": med([e for s_, a_, e in errs if s_ >= 256 and a_ < 0.02]),
+                "runs_side_ge_256_alpha_lt_0.02": sum(1 for s_, a_, _ in errs if s_ >= 256 and a_ < 0.02)}
 
     tb, db, fb = run_batched()
     tp, dp, fp = run_plain()
-    eb, nb = gamma_err(db)
-    ep, _ = gamma_err(dp)
+    eb = gamma_err(db)
+    ep = gamma_err(dp)
     total = sum(r.lattice.n for r in runs)
     return {"runs": len(runs), "particles": total, "steps": steps,
             "batched_s": tb, "plain_s": tp, "speedup": tp / tb,
             "batched_value": total * steps / tb, "plain_value": total * steps / tp,
-            "gamma_rel_err_median_batched": eb, "gamma_rel_err_median_plain": ep,
-            "runs_fitted": nb,
+            "gamma_rel_err_median_batched": eb["median_alpha_lt_0.05"],
+            "gamma_rel_err_median_plain": ep["median_alpha_lt_0.05"],
+            "gamma_rel_err_batched": eb, "gamma_rel_err_plain": ep,
+            "runs_fitted": eb["runs_fitted"],
             "runs_flagged_batched": int(np.count_nonzero(fb)),
             "runs_flagged_plain": int(np.count_nonzero(fp)),
             "note": "wall time of the step calls only; equal error = same median |gamma/gamma_root - 1|"}
 
 
+def device_leg(torch, swpic, spec, args, timed, tune=True):
+    """One workload from the lattice start on the device: launch shape tuned on
+    the state after the W warm-up steps (the autotuner restores that state),
+    then K device-timed steps, and the mean device duration of the full passes
+    of the same K steps for the roofline."""
+    lat = spec.lattice
+    n, prec, dec = lat.n, spec.precision, spec.decorated
+    jx, jv = W.jitter(lat) if lat.jitter else (None, None)
+    s = swpic.Simulation([(lat.L, spec.dt, spec.nx, n)], precision=prec, decorated=dec,
+                         diag_capacity=64)
+    try:
+        s.init_lattice(0, lat, jx, jv)
+        swpic.swpic_refresh(s.ctx)
+        s.step(args.warmup, args.diag_every)
+        if tune:
+            swpic.swpic_autotune(s.ctx, 10, None)
+        tpb, bpsm, resort = swpic.swpic_get_launch(s.ctx)
+        stages = swpic.swpic_get_pipeline(s.ctx)[1]
+        ms = timed(s, args.steps)
+        s.init_lattice(0, lat, jx, jv)
+        swpic.swpic_refresh(s.ctx)
+        s.step(args.warmup, args.diag_every)
+        swpic.swpic_set_timing(s.ctx, 1)
+        s.step(args.steps, args.diag_every)
+        pass_ms = swpic.swpic_pass_times(s.ctx)
+        swpic.swpic_set_timing(s.ctx, 0)
+    finally:
+        s.close()
+    avg = float(np.mean(pass_ms[1:-1] if len(pass_ms) > 2 else pass_ms))
+    bpp = BYTES_PER_PARTICLE[(prec, dec)]
+    peak, peak_src = measured_peak()
+    achieved = bpp * n / (avg / 1e3) / 1e9
+    return {"workload": spec.name, "particles": n, "precision": "fp%d" % prec, "decorated": dec,
+            "value": n * args.steps / (ms / 1e3), "unit": UNIT if dec else "particle-steps/s",
+            "ms_per_step": ms / args.steps,
+            "launch": {"threads_per_block": tpb, "blocks_per_sm": bpsm, "bulk_copy_stages": stages,
+                       "resort_every": resort},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "avg_launch_ms": avg,
+                         "algorithmic_bytes_per_launch": bpp * n,
+                         "kernel": "k_pass<%s, %s, atomic, deposit, diag>" % (
+                             "float" if prec == 32 else "double", "decorated" if dec else "point"),
+                         "peak_source": peak_src}}
+
+
+def method_legs(torch, swpic, args, timed):
+    """Strong Landau damping (alpha 0.5, k 0.5, 2048^2 lattice with +-0.25 cell
+    jitter, nx 512, dt 0.05): the decorated step in FP32 and in FP64, and the
+    point-particle step (decoration off, same kernels) at 16x the particles
+    (8192^2 lattice), each device-timed from the lattice start.  Then the
+    comparison at equal accuracy over t in [0, 15] (300 steps, before the
+    decorations' late growth): every run's E_amp history against the FP64
+    oracle's decorated run of the 2048^2 lattice, as a relative RMS
+    difference and as the damping rate fitted over the maxima, beside the
+    device time each run needs to reach t = 15."""
+    import oracle as O
+    from workloads import physics as ph
+    out = {"fp32_decorated": device_leg(torch, swpic, W.landau_strong(32), args, timed),
+           "fp64_decorated": device_leg(torch, swpic, W.landau_strong(64), args, timed),
+           "pic_16x": device_leg(torch, swpic, W.landau_strong(32, scale=4, decorated=False), args, timed)}
+    steps, t_end = 300, 15.0
+
+    def gpu_history(spec):
+        lat = spec.lattice
+        jx, jv = W.jitter(lat) if lat.jitter else (None, None)
+        s = swpic.Simulation([(lat.L, spec.dt, spec.nx, lat.n)], precision=spec.precision,
+                             decorated=spec.decorated, diag_capacity=steps + 8)
+        try:
+            s.init_lattice(0, lat, jx, jv)
+            swpic.swpic_refresh(s.ctx)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            s.step(steps, 1)
+            e1.record(s.stream)
+            e1.synchronize()
+            d = s.diagnostics()
+        finally:
+            s.close()
+        return d, e0.elapsed_time(e1)
+
+    spec = W.landau_strong(64)
+    lat = spec.lattice
+    jx, jv = W.jitter(lat)
+    O.set_threads(host_cores())
+    try:
+        t0 = time.perf_counter()
+        ref = O.run(O.init_lattice(lat, jx, jv), spec.nx, lat.L, spec.dt, steps, diag_every=1)["diag"]
+        t_oracle = time.perf_counter() - t0
+    finally:
+        O.set_threads(1)
+    E_ref = ref[:, 6]
+    g_ref = ph.rate_fit(ref[:, 0], E_ref, 0.0, t_end, min_sep=1.0)[0]
+    cmp = {}
+    for name, sp in (("decorated_fp32_2048^2", W.landau_strong(32)),
+                     ("pic_fp32_2048^2", W.landau_strong(32, decorated=False)),
+                     ("pic_fp32_8192^2_16x", W.landau_strong(32, scale=4, decorated=False))):
+        d, ms = gpu_history(sp)
+        E = d[: len(E_ref), 6]
+        g = ph.rate_fit(d[:, 0], d[:, 6], 0.0, t_end, min_sep=1.0)[0]
+        cmp[name] = {"particles": sp.lattice.n, "device_ms_to_t15": ms,
+                     "E_amp_rel_rms_diff_vs_oracle": float(np.sqrt(np.mean((E - E_ref) ** 2) /
+                                                                   np.mean(E_ref ** 2))),
+                     "gamma_fit": float(g), "gamma_rel_diff_vs_oracle": float(abs(g / g_ref - 1))}
+    out["equal_accuracy"] = {
+        "window": [0.0, t_end], "steps": steps, "reference": "FP64 oracle, decorated, 2048^2 lattice "
+        "(%d particles), particle loops on %d host threads, %.1f s" % (lat.n, host_cores(), t_oracle),
+        "gamma_fit_reference": float(g_ref), "runs": cmp}
+    return out
+
+
+def fp32_diag_error_leg(torch, swpic, spec, args):
+    """The error of every diagnostic of the FP32 step against the FP64 oracle
+    started from the same (FP32-representable) state: two-stream (256^2,
+    600 steps to t = 30, records every 10 steps) and the bump-on-tail
+    workload (4096^2, W + K steps from the lattice start, records every
+    step).  The error of a quantity is max over records |FP32 - FP64| over
+    its largest FP64 magnitude; the momentum, which stays near zero, is
+    measured against mass x v_rms = (2 mass kinetic)^(1/2) instead."""
+    import oracle as O
+    keys = ["mass", "momentum", "kinetic", "field_energy", "H", "E_amp"]
+
+    def compare(sp, steps, every, threads):
+        lat = sp.lattice
+        st0 = O.init_lattice(lat)
+        st = {k: v.astype(np.float32).astype(np.float64) for k, v in st0.items()}
+        del st0
+        s = swpic.Simulation([(lat.L, sp.dt, sp.nx, lat.n)], precision=32, diag_capacity=steps // every + 8)
+        try:
+            s.init_particles(st)
+            s.step(steps, every)
+            g = s.diagnostics()
+        finally:
+            s.close()
+        O.set_threads(threads)
+        try:
+            o = O.run(st, sp.nx, lat.L, sp.dt, steps, diag_every=every)["diag"]
+        finally:
+            O.set_threads(1)
+        err = {}
+        for i, k in enumerate(keys):
+            a, b = g[: len(o), i + 1], o[:, i + 1]
+            scale = np.max(np.abs(b))
+            if k == "momentum":
+                scale = float(np.sqrt(2 * o[0, 1] * o[0, 3]))
+            err[k] = float(np.max(np.abs(a - b)) / scale)
+        return {"workload": sp.name, "particles": lat.n, "steps": steps, "record_every": every,
+                "rel_error": err}
+
+    return {"two_stream": compare(W.two_stream(32), 600, 10, 1),
+            "bump_on_tail": compare(spec, args.warmup + args.steps, 1, host_cores()),
+            "note": "FP32 state and push, FP64 field energy; errors relative to each quantity's "
+                    "largest FP64 value (momentum: to (2 mass kinetic)^(1/2))"}
+
+
 def cpu_baseline_leg(spec, args):
-    cols = 64                      # 64 x 4096 = 262,144 particles
-    k = 40
-    n, dt = time_oracle(spec, cols, k, 0, args.diag_every)
-    return {"value": n * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "%d of %d lattice columns (%d particles) of %s, %d steps, single-threaded "
-                      "plain-C FP64 oracle (includes its one-time dense LU of the Poisson matrix)" %
-                      (cols, spec.lattice.nq, n, spec.name, k),
+    """The FP64 oracle on the host cores: all of them (particle loops split
+    into blocks, or_set_threads) and one, on the same bounded sample."""
+    cols = 256                     # 256 x 4096 = 1,048,576 particles
+    k = 20
+    n, dt, cores = time_oracle(spec, cols, k, 0, args.diag_every, threads=host_cores())
+    n1, dt1, _ = time_oracle(spec, cols, 5, 0, args.diag_every, threads=1)
+    how = ("%d of %d lattice columns (%d particles) of %s from the lattice start, plain-C FP64 "
+           "oracle; seconds per step = [t(K+1 steps) - t(1 step)]/K (the one-time dense LU of "
+           "each oracle run left out)" % (cols, spec.lattice.nq, n, spec.name))
+    return {"value": n * k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": how + ", K = %d, particle loops on %d host threads" % (k, cores),
+            "host_cores": host_cores(),
+            "single_core": {"value": n1 * 5 / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": how + ", K = 5, serial loops"},
             "init_kmeans": kmeans_oracle_sample(), "p2_elements": p2_oracle_sample(spec, args),
             "two_d": two_d_oracle_sample(args)}
 
@@ -715,7 +919,7 @@ def p2_oracle_sample(spec, args):
     """The oracle with the P2 field (a dense (2 nx + 1)^2 LU solve every step)
     on 64 lattice columns, 3 steps, one core."""
     cols, k = 64, 3
-    n, dt = time_oracle(spec, cols, k, 0, args.diag_every, 3)
+    n, dt, _ = time_oracle(spec, cols, k, 0, args.diag_every, 3)
     return {"value": n * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d of %d lattice columns (%d particles), %d steps, P2 field" %
                       (cols, spec.lattice.nq, n, k)}
