@@ -38,6 +38,13 @@ UNIT = "decorated particle-steps/s"
 # algorithmic bytes per particle-step of the fused pass: read Q,P,q*,p*,psi*, write Q,P,q*,p*
 BYTES_PER_PARTICLE = {(32, True): 36, (64, True): 72, (32, False): 20, (64, False): 40}
 FALLBACK_HBM_GBS = 6800.0
+# FP64 arithmetic of one decorated particle-step of the fused pass (FMA = 2):
+# element of Q (3), two half-kicks (5 each), diagnostic densities and their
+# compensated sums (13), drift (4), element, coordinate and node weights of
+# the deposit (10), the two shared-memory adds (2); without decoration the q*,
+# p* terms drop out
+FP64_FLOPS_PER_PARTICLE = {True: 42, False: 28}
+FP64_NOMINAL_TFLOPS = 1.25
 D2_MODES = {"lumped": 0, "nodal": 2, "p2": 3}      # swpic_d2_mode values
 
 
@@ -53,13 +60,21 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the deterministic-mode, e2e, ensemble and CPU-baseline legs")
-    ap.add_argument("--side", type=int, default=4096, help="lattice side (4096 = the workload)")
+    ap.add_argument("--side", type=int, default=None,
+                    help="lattice side (default: the workload's own, 4096 for bump_on_tail)")
     ap.add_argument("--launch", default=None, help="TPBxBPSM: fixed launch shape (no autotune)")
     ap.add_argument("--stages", type=int, default=None, help="bulk-copy stages (0 = register loads; no autotune)")
     ap.add_argument("--only-2d", action="store_true",
                     help="run only the 2D2V leg (K timed steps) and print its JSON object")
     ap.add_argument("--side-2d", type=int, default=4096,
                     help="2D leg: particles = side^2 = (lattice side)^4 (4096 = the 2D workload, 64^4)")
+    ap.add_argument("--workload", choices=["bump_on_tail", "landau_strong", "landau_strong_pic"],
+                    default="bump_on_tail",
+                    help="the main line's workload (bump_on_tail = the 4096^2 benchmark workload; "
+                         "landau_strong = the 2048^2 strong-Landau lattice; landau_strong_pic = its "
+                         "8192^2 point-particle form)")
+    ap.add_argument("--precision", type=int, choices=[32, 64], default=32,
+                    help="particle-state precision of the main line")
     ap.add_argument("--d2-mode", choices=list(D2_MODES), default="lumped",
                     help="phi'' of the kick: P1 field with a lumped or nodal projection, or the P2 field")
     return ap.parse_args()
@@ -195,11 +210,14 @@ def time_oracle(spec, cols, steps, warmup, diag_every, d2_mode=0, threads=1):
         lat = oracle_sample_spec(spec, cols)
         st = O.init_lattice(lat)
         if warmup > 0:
-            st = O.run(st, spec.nx, lat.L, spec.dt, warmup, diag_every=diag_every, d2_mode=d2_mode)
+            st = O.run(st, spec.nx, lat.L, spec.dt, warmup, diag_every=diag_every, d2_mode=d2_mode,
+                       decorated=spec.decorated)
         t0 = time.perf_counter()
-        O.run(st, spec.nx, lat.L, spec.dt, 1, diag_every=diag_every, d2_mode=d2_mode)
+        O.run(st, spec.nx, lat.L, spec.dt, 1, diag_every=diag_every, d2_mode=d2_mode,
+              decorated=spec.decorated)
         t1 = time.perf_counter()
-        O.run(st, spec.nx, lat.L, spec.dt, steps + 1, diag_every=diag_every, d2_mode=d2_mode)
+        O.run(st, spec.nx, lat.L, spec.dt, steps + 1, diag_every=diag_every, d2_mode=d2_mode,
+              decorated=spec.decorated)
         t2 = time.perf_counter()
     finally:
         O.set_threads(1)
@@ -237,18 +255,30 @@ def run_reference(args, spec):
 
 
 def workload_config(spec, args, resort):
+    es = 4 if spec.precision == 32 else 8
+    n_arr = 5 if spec.decorated else 3
     return {"workload": spec.name, "particles": spec.lattice.n, "lattice": [spec.lattice.nq, spec.lattice.nv],
-            "nx": spec.nx, "dt": spec.dt, "L": spec.lattice.L, "precision": "fp32 state, fp64 solve",
+            "nx": spec.nx, "dt": spec.dt, "L": spec.lattice.L,
+            "precision": "fp%d state, fp64 solve" % spec.precision, "decorated": spec.decorated,
             "deposit_mode": args.deposit_mode, "d2_mode": args.d2_mode, "diag_every": args.diag_every,
             "resort_every": resort,
-            "l2": "inputs larger than L2 (FP32 state %.0f MB > 129 MB)" % (spec.lattice.n * 20 / 1e6),
+            "l2": "inputs larger than L2 (state %.0f MB > 129 MB)" % (spec.lattice.n * es * n_arr / 1e6),
             "parallelism": "replicas (one independent run per GPU)"}
 
 
 # --------------------------------------------------------------------------
 def main():
     args = parse()
-    spec = W.bump_on_tail(precision=32, side=args.side) if args.side != 4096 else W.bump_on_tail()
+    if args.workload == "bump_on_tail":
+        spec = W.bump_on_tail(precision=args.precision, side=args.side or 4096)
+    else:
+        import dataclasses
+        spec = W.landau_strong(precision=args.precision, scale=4 if args.workload.endswith("pic") else 1,
+                               decorated=not args.workload.endswith("pic"))
+        if args.side:
+            lat_ = dataclasses.replace(spec.lattice, nq=args.side, nv=args.side)
+            spec = dataclasses.replace(spec, lattice=lat_, name="landau_strong_%dx%d%s" % (
+                args.side, args.side, "" if spec.decorated else "_pic"))
     if args.impl == "reference":
         run_reference(args, spec)
         return
@@ -268,13 +298,15 @@ def main():
     build.build()
     lat = spec.lattice
     n = lat.n
+    prec, dec = spec.precision, spec.decorated
     mode = 1 if args.deposit_mode == "deterministic" else 0
+    jx, jv = W.jitter(lat) if lat.jitter else (None, None)
 
     def make(mode_, resort, graphs=True):
-        s = swpic.Simulation([(lat.L, spec.dt, spec.nx, n)], precision=32, deposit_mode=mode_,
-                             d2_mode=D2_MODES[args.d2_mode], resort_every=max(resort, 0),
-                             use_graphs=graphs, diag_capacity=64)
-        s.init_lattice(0, lat)
+        s = swpic.Simulation([(lat.L, spec.dt, spec.nx, n)], precision=prec, decorated=dec,
+                             deposit_mode=mode_, d2_mode=D2_MODES[args.d2_mode],
+                             resort_every=max(resort, 0), use_graphs=graphs, diag_capacity=64)
+        s.init_lattice(0, lat, jx, jv)
         swpic.swpic_refresh(s.ctx)
         return s
 
@@ -283,11 +315,12 @@ def main():
     # grow without bound late in the run, so no leg runs past
     # warm-up + K steps from t = 0
     torch.cuda.synchronize()
-    init_state = [t.clone() for t in (sim.Q, sim.P, sim.qs, sim.ps, sim.psi)]
+    arrays = lambda s: [t for t in (s.Q, s.P, s.qs, s.ps, s.psi) if t is not None]
+    init_state = [t.clone() for t in arrays(sim)]
 
     def restore(s):
         torch.cuda.synchronize()
-        for dst, src in zip((s.Q, s.P, s.qs, s.ps, s.psi), init_state):
+        for dst, src in zip(arrays(s), init_state):
             dst.copy_(src)
         torch.cuda.synchronize()
         swpic.swpic_refresh(s.ctx)
@@ -299,10 +332,11 @@ def main():
         swpic.swpic_set_pipeline(sim.ctx, args.stages)
     fixed = args.launch is not None or args.stages is not None
     if args.resort < 0 and not args.no_autotune and not fixed:
-        # tune on a state like most of the timed region's (the lattice order is
-        # gone after ~300 steps), then restart from the initial state
-        sim.step(max(args.warmup, 300), args.diag_every)
-        swpic.swpic_autotune(sim.ctx, 30, None)
+        # tune on the state the timed region starts from (after the W warm-up
+        # steps), over trials as long as the timed region (at most 50 steps);
+        # the autotuner restores that state, and the run restarts from t = 0
+        sim.step(args.warmup, args.diag_every)
+        swpic.swpic_autotune(sim.ctx, max(5, min(args.steps, 50)), None)
     tpb, bpsm, resort = swpic.swpic_get_launch(sim.ctx)
     stages = swpic.swpic_get_pipeline(sim.ctx)[1]
     restore(sim)
@@ -348,14 +382,16 @@ def main():
     swpic.swpic_set_timing(sim.ctx, 0)
     full = pass_ms[1:-1] if len(pass_ms) > 2 else pass_ms
     avg_pass_ms = float(np.mean(full))
-    bpp = BYTES_PER_PARTICLE[(32, True)]
+    bpp = BYTES_PER_PARTICLE[(prec, dec)]
     achieved = bpp * n / (avg_pass_ms / 1e3) / 1e9
     peak, peak_src = measured_peak()
-    traffic = profiled_traffic("k_pass_p2_bump_on_tail_4096" if args.d2_mode == "p2" else
-                               "k_pass_bump_on_tail_4096")
+    main_line = args.workload == "bump_on_tail" and prec == 32 and (args.side or 4096) == 4096
+    traffic = (profiled_traffic("k_pass_p2_bump_on_tail_4096" if args.d2_mode == "p2" else
+                                "k_pass_bump_on_tail_4096") if main_line else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_pass<float, decorated, %s, deposit, diag%s>" % (
+                "kernel": "k_pass<%s, %s, %s, deposit, diag%s>" % (
+                    "float" if prec == 32 else "double", "decorated" if dec else "point",
                     args.deposit_mode, ", P2" if args.d2_mode == "p2" else ""),
                 "algorithmic_bytes_per_launch": bpp * n,
                 "avg_launch_ms": avg_pass_ms, "peak_source": peak_src,
@@ -363,13 +399,13 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f%d" % prec, "data": "synthetic",
             "config": dict(workload_config(spec, args, resort),
                            launch={"threads_per_block": tpb, "blocks_per_sm": bpsm,
                                    "bulk_copy_stages": stages}),
             "roofline": roofline, "gpu_launches": int(launches), "clocks": clocks}
 
-    if not args.no_extras and rank == 0:
+    if not args.no_extras and rank == 0 and main_line:
         # deterministic deposit mode, same workload
         other = 1 - mode
         s2 = make(other, resort)
@@ -425,22 +461,29 @@ def e2e_leg(torch, swpic, sim, n, args):
     the device-timed value covers (sim is at the initial state on entry)."""
     sim.step(args.warmup, args.diag_every)
     st = sim.state()
-    hin = {k: torch.from_numpy(st[k].astype(np.float32)).pin_memory() for k in ("Q", "P", "qs", "ps", "psi")}
-    hout = {k: torch.empty(n, dtype=torch.float32).pin_memory() for k in ("Q", "P", "qs", "ps")}
-    p = lambda t: t.data_ptr()
-    swpic.swpic_step_host(sim.ctx, p(hin["Q"]), p(hin["P"]), p(hin["qs"]), p(hin["ps"]), p(hin["psi"]),
-                          p(hout["Q"]), p(hout["P"]), p(hout["qs"]), p(hout["ps"]), n, 3,
-                          args.diag_every)
+    npdt, tdt = (np.float32, torch.float32) if sim.precision == 32 else (np.float64, torch.float64)
+    ins = ("Q", "P", "qs", "ps", "psi") if sim.decorated else ("Q", "P", "psi")
+    outs = ("Q", "P", "qs", "ps") if sim.decorated else ("Q", "P")
+    hin = {k: torch.from_numpy(st[k].astype(npdt)).pin_memory() for k in ins}
+    hout = {k: torch.empty(n, dtype=tdt).pin_memory() for k in outs}
+    p = lambda d, k: d[k].data_ptr() if k in d else None
+
+    def call(k_steps):
+        swpic.swpic_step_host(sim.ctx, p(hin, "Q"), p(hin, "P"), p(hin, "qs"), p(hin, "ps"), p(hin, "psi"),
+                              p(hout, "Q"), p(hout, "P"), p(hout, "qs"), p(hout, "ps"), n, k_steps,
+                              args.diag_every)
+    call(3)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    swpic.swpic_step_host(sim.ctx, p(hin["Q"]), p(hin["P"]), p(hin["qs"]), p(hin["ps"]), p(hin["psi"]),
-                          p(hout["Q"]), p(hout["P"]), p(hout["qs"]), p(hout["ps"]), n, args.steps,
-                          args.diag_every)
+    call(args.steps)
     dt = time.perf_counter() - t0
+    es = 4 if sim.precision == 32 else 8
     return {"value": n * args.steps / dt, "unit": UNIT,
-            "h2d_bytes_per_step": 20 * n / args.steps, "d2h_bytes_per_step": 16 * n / args.steps,
-            "note": "swpic_step_host on the state after the W warm-up steps: H2D of the 5 state "
-                    "arrays, field set-up, K steps, D2H of (Q, P, q*, p*), all inside the timed region"}
+            "h2d_bytes_per_step": es * len(ins) * n / args.steps,
+            "d2h_bytes_per_step": es * len(outs) * n / args.steps,
+            "note": "swpic_step_host on the state after the W warm-up steps: H2D of the %d state "
+                    "arrays, field set-up, K steps, D2H of %d arrays, all inside the timed region" %
+                    (len(ins), len(outs))}
 
 
 def kmeans_leg(torch, swpic):
@@ -500,10 +543,10 @@ def p2_leg(torch, swpic, spec, args, launch, timed):
 
     if args.resort < 0 and not args.no_autotune and args.launch is None and args.stages is None:
         # P2 adds one shared atomic per particle: tune its own launch shape and
-        # resort cadence on the state after the lattice order is gone
+        # resort cadence on the state the timed region starts from
         s = make(swpic.SWPIC_D2_P2, 64)
-        s.step(max(args.warmup, 300), args.diag_every)
-        swpic.swpic_autotune(s.ctx, 30, None)
+        s.step(args.warmup, args.diag_every)
+        swpic.swpic_autotune(s.ctx, max(5, min(args.steps, 50)), None)
         tpb, bpsm, resort = swpic.swpic_get_launch(s.ctx)
         stages = swpic.swpic_get_pipeline(s.ctx)[1]
         s.close()
@@ -757,17 +800,27 @@ def device_leg(torch, swpic, spec, args, timed, tune=True):
     bpp = BYTES_PER_PARTICLE[(prec, dec)]
     peak, peak_src = measured_peak()
     achieved = bpp * n / (avg / 1e3) / 1e9
+    kernel = "k_pass<%s, %s, atomic, deposit, diag>" % ("float" if prec == 32 else "double",
+                                                       "decorated" if dec else "point")
+    prof = {(32, False, 8192 * 8192): "k_pass_pic_landau_strong_8192"}.get((prec, dec, n))
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "avg_launch_ms": avg, "algorithmic_bytes_per_launch": bpp * n,
+            "traffic": profiled_traffic(prof) if prof else None, "kernel": kernel, "peak_source": peak_src}
+    if prec == 64:
+        # the FP64 step is bound by the FP64 pipe, not by HBM: its arithmetic
+        # (FMA = 2 flops) per particle-step against the nominal FP64 rate
+        flops = FP64_FLOPS_PER_PARTICLE[dec]
+        gf = flops * n / (avg / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": gf, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": gf / FP64_NOMINAL_TFLOPS, "flops_per_particle": flops, "avg_launch_ms": avg,
+                "kernel": kernel, "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak)",
+                "hbm_achieved_gbs": achieved, "hbm_frac": achieved / peak}
     return {"workload": spec.name, "particles": n, "precision": "fp%d" % prec, "decorated": dec,
             "value": n * args.steps / (ms / 1e3), "unit": UNIT if dec else "particle-steps/s",
             "ms_per_step": ms / args.steps,
             "launch": {"threads_per_block": tpb, "blocks_per_sm": bpsm, "bulk_copy_stages": stages,
                        "resort_every": resort},
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "avg_launch_ms": avg,
-                         "algorithmic_bytes_per_launch": bpp * n,
-                         "kernel": "k_pass<%s, %s, atomic, deposit, diag>" % (
-                             "float" if prec == 32 else "double", "decorated" if dec else "point"),
-                         "peak_source": peak_src}}
+            "roofline": roof}
 
 
 def method_legs(torch, swpic, args, timed):
@@ -775,11 +828,12 @@ def method_legs(torch, swpic, args, timed):
     jitter, nx 512, dt 0.05): the decorated step in FP32 and in FP64, and the
     point-particle step (decoration off, same kernels) at 16x the particles
     (8192^2 lattice), each device-timed from the lattice start.  Then the
-    comparison at equal accuracy over t in [0, 15] (300 steps, before the
-    decorations' late growth): every run's E_amp history against the FP64
-    oracle's decorated run of the 2048^2 lattice, as a relative RMS
-    difference and as the damping rate fitted over the maxima, beside the
-    device time each run needs to reach t = 15."""
+    comparison at equal accuracy over t in [0, 15] (300 steps): decorated and
+    point-particle runs of the same problem at several lattice sizes, each
+    E_amp history against the FP64 oracle's decorated run of the 2048^2
+    lattice (relative RMS difference), beside the device time each run needs
+    to reach t = 15, and for each error level the fewest particles with which
+    each method reaches it."""
     import oracle as O
     from workloads import physics as ph
     out = {"fp32_decorated": device_leg(torch, swpic, W.landau_strong(32), args, timed),
@@ -787,12 +841,15 @@ def method_legs(torch, swpic, args, timed):
            "pic_16x": device_leg(torch, swpic, W.landau_strong(32, scale=4, decorated=False), args, timed)}
     steps, t_end = 300, 15.0
 
-    def gpu_history(spec):
-        lat = spec.lattice
+    def gpu_history(sp):
+        lat = sp.lattice
         jx, jv = W.jitter(lat) if lat.jitter else (None, None)
-        s = swpic.Simulation([(lat.L, spec.dt, spec.nx, lat.n)], precision=spec.precision,
-                             decorated=spec.decorated, diag_capacity=steps + 8)
+        s = swpic.Simulation([(lat.L, sp.dt, sp.nx, lat.n)], precision=sp.precision,
+                             decorated=sp.decorated, diag_capacity=steps + 8)
         try:
+            s.init_lattice(0, lat, jx, jv)
+            swpic.swpic_refresh(s.ctx)
+            s.step(steps, 1)          # warm (graphs captured, clocks up)
             s.init_lattice(0, lat, jx, jv)
             swpic.swpic_refresh(s.ctx)
             torch.cuda.synchronize()
@@ -807,6 +864,12 @@ def method_legs(torch, swpic, args, timed):
             s.close()
         return d, e0.elapsed_time(e1)
 
+    def at_side(side, dec):
+        import dataclasses
+        base = W.landau_strong(32, decorated=dec)
+        return dataclasses.replace(base, lattice=dataclasses.replace(base.lattice, nq=side, nv=side),
+                                   name="landau_strong_%dx%d%s" % (side, side, "" if dec else "_pic"))
+
     spec = W.landau_strong(64)
     lat = spec.lattice
     jx, jv = W.jitter(lat)
@@ -819,21 +882,36 @@ def method_legs(torch, swpic, args, timed):
         O.set_threads(1)
     E_ref = ref[:, 6]
     g_ref = ph.rate_fit(ref[:, 0], E_ref, 0.0, t_end, min_sep=1.0)[0]
-    cmp = {}
-    for name, sp in (("decorated_fp32_2048^2", W.landau_strong(32)),
-                     ("pic_fp32_2048^2", W.landau_strong(32, decorated=False)),
-                     ("pic_fp32_8192^2_16x", W.landau_strong(32, scale=4, decorated=False))):
-        d, ms = gpu_history(sp)
-        E = d[: len(E_ref), 6]
-        g = ph.rate_fit(d[:, 0], d[:, 6], 0.0, t_end, min_sep=1.0)[0]
-        cmp[name] = {"particles": sp.lattice.n, "device_ms_to_t15": ms,
-                     "E_amp_rel_rms_diff_vs_oracle": float(np.sqrt(np.mean((E - E_ref) ** 2) /
-                                                                   np.mean(E_ref ** 2))),
-                     "gamma_fit": float(g), "gamma_rel_diff_vs_oracle": float(abs(g / g_ref - 1))}
+    rows = []
+    for dec, sides in ((True, (256, 512, 1024, 2048)), (False, (256, 512, 1024, 2048, 4096, 8192))):
+        for side in sides:
+            sp = at_side(side, dec)
+            d, ms = gpu_history(sp)
+            E = d[: len(E_ref), 6]
+            ok = bool(np.all(np.isfinite(E)))
+            err = float(np.sqrt(np.mean((E - E_ref) ** 2) / np.mean(E_ref ** 2))) if ok else None
+            rows.append({"method": "decorated" if dec else "point", "lattice": side,
+                         "particles": side * side, "device_ms_to_t15": ms, "finite": ok,
+                         "E_amp_rel_rms_err": err})
+
+    def cheapest(method, tol):
+        c = [r for r in rows if r["method"] == method and r["finite"] and r["E_amp_rel_rms_err"] <= tol]
+        return min(c, key=lambda r: r["particles"]) if c else None
+    equal = {}
+    for tol in (1e-2, 1e-3, 1e-4):
+        a, b = cheapest("decorated", tol), cheapest("point", tol)
+        equal["%g" % tol] = {"decorated": None if a is None else {k: a[k] for k in ("particles", "device_ms_to_t15")},
+                             "point": None if b is None else {k: b[k] for k in ("particles", "device_ms_to_t15")}}
     out["equal_accuracy"] = {
-        "window": [0.0, t_end], "steps": steps, "reference": "FP64 oracle, decorated, 2048^2 lattice "
-        "(%d particles), particle loops on %d host threads, %.1f s" % (lat.n, host_cores(), t_oracle),
-        "gamma_fit_reference": float(g_ref), "runs": cmp}
+        "window": [0.0, t_end], "steps": steps,
+        "reference": "FP64 oracle, decorated, 2048^2 lattice (%d particles), particle loops on %d host "
+                     "threads, %.1f s" % (lat.n, host_cores(), t_oracle),
+        "gamma_fit_reference": float(g_ref),
+        "error": "relative RMS difference of the E_amp history over the window from the reference",
+        "runs": rows,
+        "fewest_particles_within": equal,
+        "note": "GPU FP32 runs of the same problem (alpha 0.5, k 0.5, +-0.25 cell jitter, nx 512, "
+                "dt 0.05) at several lattice sizes, with and without decorations"}
     return out
 
 

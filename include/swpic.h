@@ -287,16 +287,23 @@ swpic_status swpic_kmeans_lump(const double *Qm, const double *Pm, const double 
  * device) lives in file-scope device arrays that every GPU which loads the
  * library holds until the process exits.
  *   Q, ps, psi: caller's device arrays of n elements, float (precision 32) or
- *               double (64); ps may be NULL (no decoration).
+ *               double (64); ps may be NULL (no decoration).  Q is read as a
+ *               position on the torus: values outside [0, L) are wrapped into
+ *               it as the particle pass wraps them (the arrays are not written).
  *   b:          caller's device array of nx doubles (output).
  *   L, nx:      the periodic mesh; 2 <= nx <= SWPIC_STATIC_NX_MAX, else
  *               SWPIC_EINVAL (the scratch holds at most that many nodes).
  *   stream:     work is enqueued here, asynchronously.
  * The first call on a device looks up the device addresses of the scratch
  * (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture.  Every call clears and reuses the same scratch, so calls
- * whose work overlaps on the GPU (different streams, or different host threads
- * on one device) race and must be serialised by the caller. */
+ * any stream capture.  The addresses are kept for the life of the process and do
+ * not survive a cudaDeviceReset of that device: do not call this entry point on
+ * a device after resetting it.  Every call clears and reuses the same scratch,
+ * so calls whose work overlaps on the GPU (different streams, or different host
+ * threads on one device) race and must be serialised by the caller.
+ * Errors: SWPIC_EINVAL for bad sizes or pointers; SWPIC_ECUDA when a launch
+ * fails, or when a CUDA error left pending by earlier work is found on entry
+ * (it is reported and left pending, not cleared). */
 swpic_status swpic_deposit_static(const void *Q, const void *ps, const void *psi, int64_t n,
                                   int32_t precision, double L, int32_t nx, double *b,
                                   swpic_stream stream);
@@ -318,7 +325,9 @@ swpic_status swpic_step_host(swpic_ctx *ctx, const void *Q, const void *P, const
 
 /* Synchronous.  Writes/reads the particle arrays, per-run step counters,
  * field tables and configuration as raw little-endian binary.  load requires a
- * context created with the same configuration and bound arrays. */
+ * context created with the same configuration and bound arrays; the loading
+ * context's diagnostic records are discarded (its records start at the
+ * checkpoint). */
 swpic_status swpic_save(swpic_ctx *ctx, const char *path);
 swpic_status swpic_load(swpic_ctx *ctx, const char *path);
 
@@ -332,16 +341,22 @@ swpic_status swpic_get_launch(const swpic_ctx *ctx, int32_t *threads_per_block,
                               int32_t *blocks_per_sm, int32_t *resort_every);
 
 /* How the particle pass moves particle data (no counterpart in the paper; a
- * property of this implementation).  stages = 0: each thread loads its
- * 16-byte vectors into registers.  stages = 2..8: one thread per CTA streams
- * tiles of blockDim.x vectors per array into shared memory with bulk
- * asynchronous copies (TMA), up to stages - 1 tiles ahead, and writes the
- * updated tiles back with bulk copies; the stage count actually used is the
- * largest <= stages that fits in shared memory at blocks_per_sm CTAs per SM
- * (register loads when fewer than two fit).  Results do not depend on the
- * choice beyond the deposit-order freedom of SWPIC_DEPOSIT_ATOMIC.  Default 4.
- * Invalidates captured graphs.  *effective receives the stage count that the
- * current launch shape gets (0 = register loads). */
+ * property of this implementation).  A warp works in turns of 512 bytes per
+ * array (64 FP32 or 32 FP64 two-particle vectors); lane l takes vectors l and
+ * 32 + l of a turn.  stages = 0: each thread loads its 16-byte vectors into
+ * registers, one vector ahead of the one it pushes.  stages = 2..8: every warp
+ * runs its own pipeline: lane 0 copies the warp's next turns global -> shared
+ * memory with bulk asynchronous copies (one 1-D copy per array and turn,
+ * completion counted in bytes on the stage's mbarrier), up to `stages` turns
+ * ahead; the lanes read a stage into registers, lane 0 refills it, and the
+ * updated particles are written back with plain stores.  The stage count
+ * actually used is the largest <= stages that fits in shared memory at
+ * blocks_per_sm CTAs per SM (register loads when fewer than two fit).  Both
+ * streams give every thread the same particles in the same order, so results
+ * do not depend on the choice beyond the deposit-order freedom of
+ * SWPIC_DEPOSIT_ATOMIC.  Default 4.  Invalidates captured graphs.
+ * *effective receives the stage count that the current launch shape gets
+ * (0 = register loads). */
 swpic_status swpic_set_pipeline(swpic_ctx *ctx, int32_t stages);
 swpic_status swpic_get_pipeline(const swpic_ctx *ctx, int32_t *requested, int32_t *effective);
 
@@ -360,6 +375,21 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
  * (synchronous). */
 swpic_status swpic_set_timing(swpic_ctx *ctx, int32_t enable);
 swpic_status swpic_pass_times(swpic_ctx *ctx, float *ms, int32_t max_passes, int32_t *n_passes);
+
+/* Failure-path hook for tests (no counterpart in the paper): every wait of
+ * the bulk-copy stream for its copies is bounded, and one that runs out flags
+ * the run (reported by swpic_synchronize as SWPIC_ETIMEOUT, bit 4 of
+ * swpic_run_status); the warp then waits, again bounded, for the copies it has
+ * in flight, and its CTA leaves the pass.  stall_warp >= 0 makes that warp
+ * (grid-wide index blockIdx * warps per block + warp) leave the stage of its
+ * first turn unarmed in every later pass: no copy is issued into it, so its
+ * wait can only run out, while every copy that is issued still lands.
+ * wait_limit_ns bounds each wait (0 = the default of 1 s).  A pass that timed
+ * out leaves the run's field stale; swpic_refresh recovers it.  stall_warp =
+ * -1 with wait_limit_ns = 0 restores normal operation.  Invalidates captured
+ * graphs.  Only the bulk-copy stream waits (swpic_set_pipeline with >= 2
+ * stages that fit). */
+swpic_status swpic_set_wait_test(swpic_ctx *ctx, int32_t stall_warp, int64_t wait_limit_ns);
 
 /* Number of kernel launches this context has issued so far (a graph replay
  * counts each kernel node it contains). */

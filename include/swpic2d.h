@@ -148,7 +148,9 @@ swpic_status swpic2d_synchronize(swpic2d_ctx *ctx);
  * context with the same precision, decoration flag, particle count, mesh,
  * domain and dt (SWPIC_EINVAL otherwise, SWPIC_EIO when unreadable),
  * restores the step count and takes the field of the state (as
- * swpic2d_refresh).  Diagnostic records stay in the context that made them. */
+ * swpic2d_refresh).  The loading context's diagnostic records are discarded:
+ * its records start at the checkpoint (the records before it stay with the
+ * context that made them). */
 swpic_status swpic2d_save(swpic2d_ctx *ctx, const char *path);
 swpic_status swpic2d_load(swpic2d_ctx *ctx, const char *path);
 

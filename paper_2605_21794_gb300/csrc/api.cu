@@ -87,6 +87,8 @@ struct swpic_ctx {
     std::string err;
     std::map<std::string, GraphEntry> graph_cache;
     bool timing = false;
+    unsigned long long wait_limit_ns = 1000000000ull;   // 1 s
+    int32_t stall_warp = -1;
     std::vector<cudaEvent_t> events;
     int n_timed = 0;
     int64_t launches = 0;
@@ -202,6 +204,8 @@ PassArgs base_args(swpic_ctx *ctx) {
     a.ring_count = ctx->d_ring_count;
     a.ring_cap = ctx->cap;
     a.err = ctx->d_err;
+    a.wait_limit_ns = ctx->wait_limit_ns;
+    a.stall_warp = ctx->stall_warp;
     return a;
 }
 
@@ -1017,6 +1021,10 @@ swpic_status swpic_load(swpic_ctx *ctx, const char *path) {
     }
     std::vector<long long> steps(ctx->R);
     if (std::fread(steps.data(), sizeof(long long), ctx->R, f) != (size_t)ctx->R) return bad("truncated steps");
+    // the bound arrays are overwritten below with synchronous copies: work still
+    // queued on the context's stream (earlier steps) must finish first
+    const cudaError_t se = cudaStreamSynchronize(ctx->stream);
+    if (se != cudaSuccess) { std::fclose(f); return fail_cuda(ctx, "load", se); }
     const size_t es = elem_size(ctx->prec);
     std::vector<unsigned char> buf((size_t)ctx->N * es);
     for (int k = 0; k < 5; ++k) {
@@ -1067,6 +1075,16 @@ swpic_status swpic_get_pipeline(const swpic_ctx *ctx, int32_t *requested, int32_
     if (!ctx) return SWPIC_EINVAL;
     if (requested) *requested = ctx->pipe;
     if (effective) *effective = pass_stages(ctx);
+    return SWPIC_OK;
+}
+
+swpic_status swpic_set_wait_test(swpic_ctx *ctx, int32_t stall_warp, int64_t wait_limit_ns) {
+    if (!ctx) return SWPIC_EINVAL;
+    if (stall_warp < -1 || wait_limit_ns < 0 || wait_limit_ns > 10000000000ll)
+        return fail(ctx, SWPIC_EINVAL, "stall_warp must be >= -1 and wait_limit_ns in [0, 1e10]");
+    ctx->stall_warp = stall_warp;
+    ctx->wait_limit_ns = wait_limit_ns ? (unsigned long long)wait_limit_ns : 1000000000ull;
+    clear_graphs(ctx);
     return SWPIC_OK;
 }
 

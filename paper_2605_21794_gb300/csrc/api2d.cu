@@ -548,6 +548,7 @@ swpic_status swpic2d_load(swpic2d_ctx *ctx, const char *path) {
     std::fclose(f);
     ctx->step = h.step;
     ctx->last_rec = h.last_rec;
+    ctx->n_rec = 0;               // the records start at the checkpoint, as in the 1D load
     return swpic2d_refresh(ctx);
 }
 

@@ -77,14 +77,14 @@ __device__ __forceinline__ Geo<double> geo_of(const RunDev &r, double) {
 
 // Position inside element i, xi = Q nx/L - i.  The element index itself is
 // decided by the single rounded product (the key definition); xi is formed
-// with the rounding error of that product and the low part of nx/L added
+// as Q inv_h - i in one fused operation (the result is below 1, so it is
+// rounded at the ulp of xi, not of Q nx/L), with the low part of nx/L added
 // back, so an FP32 state does not see the ~nx ulp bias of fl32(nx/L) near
-// Q = L (the error of xi stays at the ulp of xi, not of Q nx/L).
-// p = fl(Q inv_h) is the rounded product the element was decided from, fi the
-// element index as a float.
+// Q = L.  fi is the element index as a float (p, the rounded product, is not
+// needed).
 __device__ __forceinline__ float xi_of(float Q, float p, float fi, const Geo<float> &G) {
-    const float err = fmaf(Q, G.inv_h, -p);      // exact rounding error of the product
-    return (p - fi) + fmaf(Q, G.inv_h_lo, err);
+    (void)p;
+    return fmaf(Q, G.inv_h_lo, fmaf(Q, G.inv_h, -fi));
 }
 __device__ __forceinline__ double xi_of(double, double p, double fi, const Geo<double> &) {
     return p - fi;
@@ -265,23 +265,6 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 v, int o) {
 __device__ __forceinline__ double i128_to_double(__int128 v) {
     return (double)(long long)(v >> 64) * 18446744073709551616.0 + (double)(unsigned long long)v;
 }
-// nearest float to an unsigned 64-bit integer (ties to even), integer operations only
-__device__ __forceinline__ float ull_to_float(unsigned long long ax) {
-    if (ax == 0ull) return 0.0f;
-    const int lz = __clzll((long long)ax);
-    const unsigned long long m = ax << lz;
-    unsigned mant = (unsigned)(m >> 40);
-    const unsigned long long rest = m & 0xFFFFFFFFFFull, half = 0x8000000000ull;
-    mant += (rest > half || (rest == half && (mant & 1u))) ? 1u : 0u;
-    return __uint_as_float(((unsigned)(190 - lz) << 23) + (mant - 0x800000u));
-}
-// a non-negative int128 as a float (the low bits beyond 64 are dropped first)
-__device__ __forceinline__ float u128_to_float(__int128 v) {
-    const unsigned long long hi = (unsigned long long)(v >> 64);
-    if (hi == 0ull) return ull_to_float((unsigned long long)v);
-    const int sh = 64 - __clzll((long long)hi);
-    return scalbnf(ull_to_float((unsigned long long)(v >> sh)), sh);
-}
 // nearest float to a 64-bit integer (ties to even, as a conversion rounds),
 // from integer operations only: the conversion instruction runs on the
 // narrow FP64/conversion pipe of this GPU
@@ -407,40 +390,19 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
     //    Thread 0 then computes the field energy about the reference while
     //    the other warps build the table: sum (e - m)^2 = sum (e - c)^2 -
     //    nx (m - c)^2 (no cancellation while c is near m), W = (h/2) sum e^2
-    //    2^-2k, E_amp.  No FP64 division or square root in the FP32 path:
-    //    they are long serial sequences on this GPU's narrow FP64 pipe.
+    //    2^-2k, E_amp, in FP64 for either state precision (the sums are exact
+    //    integers; only their conversion and the products round).
     if (tid == 0) {
         __int128 e2sum = 0;
         for (int w = 0; w < nw; ++w) e2sum += sh_q[1][w];
-        bool done = false;
-        if (sizeof(T) == 4) {
-            // FP32 state: FP32 diagnostics from integer-converted sums (no FP64
-            // latency chain), unless the reference is far from the new mean
-            const float e2f = u128_to_float(e2sum);
-            const float d8f = (ll_to_float(mean_i - c) + ll_to_float(mrem) * R.inv_nxf) * (1.0f / 256.0f);
-            const float sub = (float)nx * d8f * d8f;
-            if (sub <= 0.25f * e2f) {
-                const int ke = (int)((__double_as_longlong(inv) >> 52) & 0x7ff) - 1023 + 8;   // inv 2^8 = 2^ke
-                const float E2f = scalbnf(e2f - sub, 2 * ke);
-                a.field_diag[2 * r] = (double)(0.5f * R.hf * E2f);
-                a.field_diag[2 * r + 1] = (double)sqrtf(E2f * R.inv_nxf);
-                if (!isfinite(E2f)) atomicOr(a.err + r, kErrNonFinite);
-                done = true;
-            }
-        }
-        if (!done) {
-            const double d8 = ((double)(mean_i - c) + (double)mrem * R.inv_nx) * (1.0 / 256.0);
-            const double sc = inv * 256.0;                      // undo the >> 8
-            double E2 = (i128_to_double(e2sum) - (double)nx * d8 * d8) * sc * sc;
-            if (E2 < 0.0) E2 = 0.0;
-            const double W = 0.5 * R.h * E2;
-            double Ea;
-            if (sizeof(T) == 4) Ea = (double)sqrtf((float)(E2 * R.inv_nx));   // FP32 state: FP32 precision
-            else Ea = sqrt(E2 * R.inv_nx);
-            a.field_diag[2 * r] = W;
-            a.field_diag[2 * r + 1] = Ea;
-            if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
-        }
+        const double d8 = ((double)(mean_i - c) + (double)mrem * R.inv_nx) * (1.0 / 256.0);
+        const double sc = inv * 256.0;                      // undo the >> 8
+        double E2 = (i128_to_double(e2sum) - (double)nx * d8 * d8) * sc * sc;
+        if (E2 < 0.0) E2 = 0.0;
+        const double W = 0.5 * R.h * E2;
+        a.field_diag[2 * r] = W;
+        a.field_diag[2 * r + 1] = sqrt(E2 * R.inv_nx);
+        if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
         a.gauge[r] = mean_i;
     }
     // the table nodes go to the threads after warp 0 (all threads if there is one warp)
@@ -586,9 +548,9 @@ __device__ __forceinline__ void mesh_add(int key, T a0, T a1, void *mesh, T scal
 }
 
 // Warp-aggregated deposit: lanes holding the same element in consecutive lanes
-// form a segment; a segmented suffix sum (5 shuffle steps, fixed order) gives
-// the segment's first lane the segment total, and only that lane touches the
-// shared mesh.  When no lane shares its element with the lane before (a
+// form a segment; a segmented suffix sum (up to 5 shuffle steps, fixed order)
+// gives the segment's first lane the segment total, and only that lane touches
+// the shared mesh.  When no lane shares its element with the lane before (a
 // disordered plasma) the shuffles are skipped and every lane adds its own
 // value.  key < 0 marks an empty slot.  All 32 lanes must call this.
 template <typename T, int MODE>
@@ -602,8 +564,11 @@ __device__ __forceinline__ void warp_deposit(int key, T a0, T a1, void *mesh, T 
     if (heads != full) {
         const unsigned above = (lane == 31) ? 0u : (heads & (0xffffffffu << (lane + 1)));
         const int seg_end = above ? (__ffs(above) - 2) : 31;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
+        // rounds only up to the longest segment (a uniform trip count): a disordered
+        // warp with short segments skips most of the five shuffle rounds
+        const int span = __reduce_max_sync(full, (unsigned)(seg_end - lane));   // longest segment - 1
+#pragma unroll 1
+        for (int off = 1; off <= span; off <<= 1) {
             const T b0 = __shfl_down_sync(full, a0, off);
             const T b1 = __shfl_down_sync(full, a1, off);
             if (lane + off <= seg_end) { a0 += b0; a1 += b1; }
@@ -703,6 +668,148 @@ struct VecOut {
     }
 };
 
+// ---------------------------------------------------------------------------
+// FP32 two-particle vectors in packed arithmetic.  Compute capability 10.x
+// executes add, sub, mul and fma on a pair of FP32 values (.f32x2) as one
+// instruction; each half is rounded exactly as the scalar operation would be,
+// so the push below gives bit for bit the results of push_one on each
+// particle (up to the sign of an exactly zero deposit weight), with half the
+// FP32 instructions.  min, max and negation have no packed form: the clamps
+// of the element index stay scalar, and negated operands are formed as 0 - x.
+// ---------------------------------------------------------------------------
+typedef unsigned long long f2p;          // two packed floats, low half = first particle
+__device__ __forceinline__ f2p pk2(float a, float b) {
+    f2p r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f2p r, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
+    f2p d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
+    f2p d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p add2(f2p a, f2p b) {
+    f2p d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
+    f2p d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p add2_rd(f2p a, f2p b) {
+    f2p d;
+    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f2p splat2(float a) { return pk2(a, a); }
+
+// element index of both halves of p = Q nx/L (see elem_index_c): clamp,
+// 2^23 + p rounded down, bit pattern minus that of 2^23; fi = floor(p) as floats
+__device__ __forceinline__ void elem2(f2p p, float cmax, int &i0, int &i1, f2p &fi) {
+    float a, b;
+    upk2(p, a, b);
+    a = fminf(fmaxf(a, 0.0f), cmax);
+    b = fminf(fmaxf(b, 0.0f), cmax);
+    const f2p y = add2_rd(pk2(a, b), splat2(8388608.0f));
+    fi = sub2(y, splat2(8388608.0f));
+    float ya, yb;
+    upk2(y, ya, yb);
+    i0 = __float_as_int(ya) - 0x4B000000;
+    i1 = __float_as_int(yb) - 0x4B000000;
+}
+
+template <bool DEC, bool DEP, bool DIAG, int D2>
+__device__ __forceinline__ void push_vector_f2(float2 &q, float2 &p, float2 &x, float2 &y, const float2 &m,
+                                               const float2 *s_tab, int nx, const Geo<float> &G, float k1,
+                                               float k2, float kd, Thread<float> &th, VecOut<float> &o) {
+    const f2p INVH = splat2(G.inv_h);
+    f2p Q = pk2(q.x, q.y), P = pk2(p.x, p.y), W = pk2(m.x, m.y);
+    f2p QS = DEC ? pk2(x.x, x.y) : 0ull, PS = DEC ? pk2(y.x, y.y) : 0ull;
+    // gather at the old position: phi_h' and phi_h'' of the element
+    int i0, i1;
+    f2p FI;
+    elem2(mul2(Q, INVH), G.cmax, i0, i1, FI);
+    const float2 t0 = s_tab[i0], t1 = s_tab[i1];
+    const f2p D1 = pk2(t0.x, t1.x);
+    f2p D2v = pk2(t0.y, t1.y);
+    if (DEC && D2 == SWPIC_D2_NODAL) {
+        // xi = Q nx/L - i with the low part of nx/L added back; phi'' linear in xi
+        const f2p XI = fma2(Q, splat2(G.inv_h_lo), fma2(Q, INVH, sub2(splat2(0.0f), FI)));
+        const float g0 = s_tab[i0 + 1 == nx ? 0 : i0 + 1].y, g1 = s_tab[i1 + 1 == nx ? 0 : i1 + 1].y;
+        D2v = fma2(XI, sub2(pk2(g0, g1), D2v), D2v);
+    }
+    // closing half-kick of the previous step
+    P = fma2(splat2(-k1), D1, P);
+    if (DEC) QS = fma2(mul2(splat2(k1), PS), D2v, QS);
+    if (DIAG) {
+        const f2p DM = DEC ? fma2(W, P, QS) : mul2(W, P);
+        const f2p WP = mul2(mul2(splat2(0.5f), W), P);
+        const f2p DK = DEC ? fma2(WP, P, mul2(QS, P)) : mul2(WP, P);
+        float a, b;
+        upk2(DM, a, b);
+        const float vm = a + b;
+        upk2(DK, a, b);
+        const float vk = a + b;
+        th.mom.add(vm);
+        th.kin.add(vk);
+    }
+    // opening half-kick of the next step
+    P = fma2(splat2(-k2), D1, P);
+    if (DEC) QS = fma2(mul2(splat2(k2), PS), D2v, QS);
+    // drift, with the periodic wrap of each half (drift_wrap) when it leaves [0, L)
+    const f2p Q0 = Q;
+    Q = fma2(splat2(kd), P, Q);
+    {
+        float a, b, qa, qb, pa, pb;
+        upk2(Q, a, b);
+        // 0 <= q < L exactly  <=>  bits(q) < bits(Ltop) compared as unsigned (a
+        // negative q has the sign bit set; Ltop is fl32(L), or the next float
+        // above it when L lies above fl32(L))
+        const float Ltop = (G.L_lo > 0.0f) ? __int_as_float(__float_as_int(G.L) + 1) : G.L;
+        const unsigned lt = __float_as_uint(Ltop);
+        if (__float_as_uint(a) >= lt || __float_as_uint(b) >= lt) {
+            upk2(Q0, qa, qb);
+            upk2(P, pa, pb);
+            if (__float_as_uint(a) >= lt) a = drift_wrap(qa, pa, kd, G);
+            if (__float_as_uint(b) >= lt) b = drift_wrap(qb, pb, kd, G);
+            Q = pk2(a, b);
+        }
+    }
+    if (DEC) PS = fma2(splat2(-kd), QS, PS);
+    if (DEP) {
+        f2p FK;
+        elem2(mul2(Q, INVH), G.cmax, o.key[0], o.key[1], FK);
+        const f2p XI = fma2(Q, splat2(G.inv_h_lo), fma2(Q, INVH, sub2(splat2(0.0f), FK)));
+        f2p W0, W1;
+        if (DEC) {
+            const f2p DQ = mul2(PS, INVH);
+            W0 = fma2(W, sub2(splat2(1.0f), XI), DQ);
+            W1 = fma2(W, XI, sub2(splat2(0.0f), DQ));
+        } else {
+            W0 = mul2(W, sub2(splat2(1.0f), XI));
+            W1 = mul2(W, XI);
+        }
+        upk2(W0, o.w0[0], o.w0[1]);
+        upk2(W1, o.w1[0], o.w1[1]);
+    }
+    upk2(Q, q.x, q.y);
+    upk2(P, p.x, p.y);
+    if (DEC) {
+        upk2(QS, x.x, x.y);
+        upk2(PS, y.x, y.y);
+    }
+}
+
 // Push the particles of one 16-byte vector in place; their diagnostics go to
 // th (one compensated add per vector), their deposit slots to o.
 template <typename T, bool DEC, bool DEP, bool DIAG, int D2>
@@ -711,6 +818,11 @@ __device__ __forceinline__ void push_vector(typename Vec16<T>::type &q, typename
                                             const typename Vec16<T>::type &m,
                                             const typename Vec2<T>::type *s_tab, int nx, const Geo<T> &G,
                                             T k1, T k2, T kd, Thread<T> &th, VecOut<T> &o) {
+    if constexpr (sizeof(T) == 4 && D2 != SWPIC_D2_P2) {
+        // FP32 P1 field: both particles of the vector in packed arithmetic
+        push_vector_f2<DEC, DEP, DIAG, D2>(q, p, x, y, m, s_tab, nx, G, k1, k2, kd, th, o);
+        return;
+    }
     constexpr int VW = Vec16<T>::n;
     T *Q = reinterpret_cast<T *>(&q), *P = reinterpret_cast<T *>(&p);
     T *X = reinterpret_cast<T *>(&x), *Y = reinterpret_cast<T *>(&y);
@@ -895,11 +1007,10 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
 // arithmetic, and the copy engine keeps S turns per warp in flight without
 // holding registers.
 //
-// Every wait is bounded (kWaitLimitNs of wall time); a wait that runs out
-// sets kErrTimeout in the run's flag word, and the warp stops, waits (again
-// bounded) for its copies in flight, and the CTA leaves the kernel after the
-// segment.
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;   // 1 s
+// Every wait is bounded (PassArgs::wait_limit_ns of wall time, 1 s unless a
+// test shortens it); a wait that runs out sets kErrTimeout in the run's flag
+// word, and the warp stops, waits (again bounded) for its copies in flight,
+// and the CTA leaves the kernel after the segment.
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -927,12 +1038,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "memory");
     return done != 0;
 }
-// true when the phase with this parity completed; false after kWaitLimitNs
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+// true when the phase with this parity completed; false after limit_ns
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, unsigned long long limit_ns) {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (!mbar_try_wait(bar, parity))
-        if (global_ns() - t0 > kWaitLimitNs) return false;
+        if (global_ns() - t0 > limit_ns) return false;
     return true;
 }
 __device__ __forceinline__ void bulk_load(void *dst_smem, const void *src, uint32_t bytes, uint64_t *bar) {
@@ -1028,8 +1139,13 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
     const int S = pp.S;
 
     auto turn_vecs = [&](int k) -> int { return (int)min((int64_t)TurnVecs<T>::n, v1 - (wbase + (int64_t)k * stride)); };
+    // test hook: the chosen warp leaves the stage of its first turn unarmed (no
+    // arrival, no copy), so that stage's wait can only run out
+    const bool stall = a.stall_warp >= 0 && pp.seq == 0 &&
+                       (int)(blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) == a.stall_warp;
     auto issue = [&](int k) {            // lane 0 only
         const uint32_t q = pp.seq + (uint32_t)k;
+        if (stall && q == 0) return;
         unsigned char *st = pp.base + (size_t)(q % S) * NA * ARR;
         uint64_t *bar = pp.bar + (q % S);
         const uint32_t nb = (uint32_t)turn_vecs(k) * (uint32_t)sizeof(V);
@@ -1047,7 +1163,7 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
     for (; k < nturn; ++k) {
         const uint32_t q = pp.seq + (uint32_t)k;
         const V *sv = reinterpret_cast<const V *>(pp.base + (size_t)(q % S) * NA * ARR);
-        const bool arrived = mbar_wait_bounded(pp.bar + (q % S), (q / S) & 1u);
+        const bool arrived = mbar_wait_bounded(pp.bar + (q % S), (q / S) & 1u, a.wait_limit_ns);
         if (!__all_sync(full, arrived)) {
             if (lane == 0) { atomicOr(err, kErrTimeout); *s_abort = 1; }
             ok = false;
@@ -1072,12 +1188,21 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
             if (lane == 0) issue(k + S);
             ++issued;
         }
+        // push both vectors of the turn first (their table loads and arithmetic
+        // interleave), then store them, then deposit them
+        VecOut<T> o[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            VecOut<T> o;
             if (have[u]) {
                 push_vector<T, DEC, DEP, DIAG, D2>(qv[u], pv[u], xv[u], yv[u], mv[u], s_tab, nx, G, k1, k2, kd,
-                                                   th, o);
+                                                   th, o[u]);
+            } else {
+                o[u].clear();
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            if (have[u]) {
                 const int64_t vv = wbase + (int64_t)k * stride + 32 * u + lane;
                 reinterpret_cast<V *>(Qo)[vv] = qv[u];
                 reinterpret_cast<V *>(Po)[vv] = pv[u];
@@ -1086,17 +1211,18 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
                     reinterpret_cast<V *>(pso)[vv] = yv[u];
                 }
                 if (wpsi) reinterpret_cast<V *>(wo)[vv] = mv[u];
-            } else {
-                o.clear();
             }
-            if (DEP) deposit_vector<T, MODE, D2 == SWPIC_D2_P2>(o, s_mesh, s_mesh_m, scale, err);
+        }
+        if (DEP) {
+#pragma unroll
+            for (int u = 0; u < U; ++u) deposit_vector<T, MODE, D2 == SWPIC_D2_P2>(o[u], s_mesh, s_mesh_m, scale, err);
         }
     }
     if (!ok && lane == 0) {
         // drain: wait (bounded) for every copy still in flight into this warp's stages
         for (int u = k; u < issued; ++u) {
             const uint32_t qq = pp.seq + (uint32_t)u;
-            mbar_wait_bounded(pp.bar + (qq % S), (qq / S) & 1u);
+            mbar_wait_bounded(pp.bar + (qq % S), (qq / S) & 1u, a.wait_limit_ns);
         }
     }
     pp.seq += (uint32_t)issued;

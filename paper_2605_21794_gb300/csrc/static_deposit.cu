@@ -14,10 +14,12 @@
 // accumulator plus two doubles for the weight bound: 32 KB + 16 B per device.
 //
 // Arithmetic is the same as the context path's deposit: b_j = sum_a psi*_a
-// phi_j(Q_a) - p*_a phi_j'(Q_a) on a periodic P1 mesh, element decided by
-// floor(Q nx/L) in the state's precision, per-thread contributions converted to
-// 64-bit fixed point with a power-of-two scale fixed by sum |psi*| + 2 sum |p*|/h,
-// and added exactly with integer atomics.
+// phi_j(Q_a) - p*_a phi_j'(Q_a) on a periodic P1 mesh, positions wrapped into
+// [0, L) first (in FP32 against L = fl32(L) + the low part, as the particle pass
+// wraps), element decided by floor(Q nx/L) in the state's precision,
+// per-thread contributions converted to 64-bit fixed point with a power-of-two
+// scale fixed by sum |psi*| + 2 sum |p*|/h, and added exactly with integer
+// atomics.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -76,6 +78,33 @@ __device__ __forceinline__ double xi_t(double, double p, double fi, double, doub
     return p - fi;
 }
 
+// Periodic wrap into [0, L).  FP64: Q - L floor(Q/L) with the round-up case
+// (a result equal to L) mapped to 0.  FP32: L is not a float, so it is carried
+// as L_hi + L_lo (L_hi = fl32(L)); a position is inside when Q >= 0 and
+// Q - L_hi < L_lo (Q - L_hi is exact near L), and a position one period off is
+// shifted with both parts, so wrapped particles are not moved by L - fl32(L).
+__device__ __forceinline__ double wrap_t(double q, double L, double, double) {
+    if (q >= 0.0 && q < L) return q;
+    double w = __dsub_rn(q, __dmul_rn(L, floor(q / L)));     // unfused, as the pass rounds it
+    if (w >= L) w -= L;
+    if (w < 0.0) w += L;
+    return w;
+}
+__device__ __forceinline__ bool inside_t(float q, float L_hi, float L_lo) {
+    return q >= 0.0f && (q - L_hi) < L_lo;
+}
+__device__ __forceinline__ float wrap_t(float q, float L_hi, float L_lo, float inv_L) {
+    if (inside_t(q, L_hi, L_lo) || q != q) return q;
+    float w = (q >= 0.0f) ? (q - L_hi) - L_lo : (q + L_hi) + L_lo;   // one period off
+    if (inside_t(w, L_hi, L_lo)) return w;
+    const float k = floorf(w * inv_L);                                 // several periods
+    w = fmaf(-k, L_lo, fmaf(-k, L_hi, w));
+    if (w >= 0.0f && !inside_t(w, L_hi, L_lo)) w = (w - L_hi) - L_lo;
+    if (w < 0.0f) w = (w + L_hi) + L_lo;
+    if (!inside_t(w, L_hi, L_lo)) w = (w < 0.0f) ? 0.0f : (w - L_hi) - L_lo;
+    return w < 0.0f ? 0.0f : w;
+}
+
 __device__ __forceinline__ double fixed_scale(const double *bound, double inv_h) {
     const double m = bound[0] + 2.0 * bound[1] * inv_h;
     int k = 58;
@@ -86,14 +115,15 @@ __device__ __forceinline__ double fixed_scale(const double *bound, double inv_h)
 
 template <typename T>
 __global__ void k_static_deposit(const T *Q, const T *ps, const T *psi, int64_t n, T inv_h, T inv_h_lo,
-                                 int nx, const double *bound, unsigned long long *acc) {
+                                 T L_hi, T L_lo, T inv_L, int nx, const double *bound,
+                                 unsigned long long *acc) {
     extern __shared__ unsigned long long s_mesh[];           // nx + 1 words
     for (int j = threadIdx.x; j <= nx; j += blockDim.x) s_mesh[j] = 0ull;
     __syncthreads();
     const double scale = fixed_scale(bound, (double)inv_h);
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n;
          k += (int64_t)gridDim.x * blockDim.x) {
-        const T q = Q[k];
+        const T q = wrap_t(Q[k], L_hi, L_lo, inv_L);
         const T p = q * inv_h;
         T fi;
         const int i = swpic::elem_index(p, nx, fi);
@@ -121,15 +151,20 @@ __global__ void k_static_finish(const unsigned long long *acc, const double *bou
 }
 
 // once per device, with that device current: the device addresses of the
-// scratch arrays (their host-side names are not device addresses)
+// scratch arrays (their host-side names are not device addresses).  They are
+// kept for the life of the process: a cudaDeviceReset unloads this code from
+// the device, and the kept addresses are not valid after it.
 swpic_status static_setup(StaticPtrs *out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return SWPIC_ECUDA;
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_ready[dev]) {
         StaticPtrs p;
-        if (cudaGetSymbolAddress((void **)&p.acc, g_acc) != cudaSuccess) return SWPIC_ECUDA;
-        if (cudaGetSymbolAddress((void **)&p.bound, g_bound) != cudaSuccess) return SWPIC_ECUDA;
+        if (cudaGetSymbolAddress((void **)&p.acc, g_acc) != cudaSuccess ||
+            cudaGetSymbolAddress((void **)&p.bound, g_bound) != cudaSuccess) {
+            cudaGetLastError();          // this call's own error, reported by the status
+            return SWPIC_ECUDA;
+        }
         g_ptrs[dev] = p;
         g_ready[dev] = true;
     }
@@ -146,26 +181,35 @@ extern "C" swpic_status swpic_deposit_static(const void *Q, const void *ps, cons
     if (!(L > 0.0) || !std::isfinite(L) || n < 0 || !b) return SWPIC_EINVAL;
     if (precision != SWPIC_F32 && precision != SWPIC_F64) return SWPIC_EINVAL;
     if (n > 0 && (!Q || !psi)) return SWPIC_EINVAL;
+    // an error left pending by earlier work is reported, not cleared (it is
+    // not this call's to consume); past this point every launch error is ours
+    if (cudaPeekAtLastError() != cudaSuccess) return SWPIC_ECUDA;
     StaticPtrs p;
     swpic_status st = static_setup(&p);
     if (st != SWPIC_OK) return st;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const double inv_h = (double)nx / L;
     k_static_clear<<<(nx + 256) / 256, 256, 0, s>>>(p.acc, p.bound, nx);
+    if (cudaGetLastError() != cudaSuccess) return SWPIC_ECUDA;
     if (n > 0) {
         const int grid = (int)((n + 255) / 256 < 1216 ? (n + 255) / 256 : 1216);
         const size_t smem = (size_t)(nx + 1) * 8;
         if (precision == SWPIC_F64) {
             k_static_bound<double><<<grid, 256, 0, s>>>((const double *)ps, (const double *)psi, n, p.bound);
+            if (cudaGetLastError() != cudaSuccess) return SWPIC_ECUDA;
             k_static_deposit<double><<<grid, 256, smem, s>>>((const double *)Q, (const double *)ps,
-                                                             (const double *)psi, n, inv_h, 0.0, nx, p.bound,
-                                                             p.acc);
+                                                             (const double *)psi, n, inv_h, 0.0, L, 0.0,
+                                                             1.0 / L, nx, p.bound, p.acc);
         } else {
             k_static_bound<float><<<grid, 256, 0, s>>>((const float *)ps, (const float *)psi, n, p.bound);
+            if (cudaGetLastError() != cudaSuccess) return SWPIC_ECUDA;
             const float hi = (float)inv_h, lo = (float)(inv_h - (double)hi);
+            const float L_hi = (float)L, L_lo = (float)(L - (double)L_hi);
             k_static_deposit<float><<<grid, 256, smem, s>>>((const float *)Q, (const float *)ps,
-                                                            (const float *)psi, n, hi, lo, nx, p.bound, p.acc);
+                                                            (const float *)psi, n, hi, lo, L_hi, L_lo,
+                                                            (float)(1.0 / L), nx, p.bound, p.acc);
         }
+        if (cudaGetLastError() != cudaSuccess) return SWPIC_ECUDA;
     }
     k_static_finish<<<1, 256, 0, s>>>(p.acc, p.bound, inv_h, nx, b);
     return cudaGetLastError() == cudaSuccess ? SWPIC_OK : SWPIC_ECUDA;

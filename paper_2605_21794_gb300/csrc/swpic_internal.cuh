@@ -100,6 +100,9 @@ struct PassArgs {
     int32_t *ring_count;      // [R]
     int32_t ring_cap;
     int32_t *err;             // [R] per-run anomaly flags (kErr* bits)
+    unsigned long long wait_limit_ns;   // bound of every mbarrier wait of the bulk-copy stream
+    int32_t stall_warp;       // test hook: this warp (grid-wide index) never arms its first
+                              // stage, so its first wait runs out; -1 = none
 };
 
 // shared-memory bytes of the pass kernel / the per-run solve for a given max nx

@@ -23,6 +23,7 @@ SWPIC_F32, SWPIC_F64 = 32, 64
 SWPIC_DEPOSIT_ATOMIC, SWPIC_DEPOSIT_DETERMINISTIC = 0, 1
 SWPIC_D2_LUMPED, SWPIC_D2_NODAL, SWPIC_D2_P2 = 0, 2, 3
 SWPIC_NX_MAX = 4096
+SWPIC_STATIC_NX_MAX = 4096
 
 
 class swpic_config(C.Structure):
@@ -111,6 +112,7 @@ SIGNATURES = {
     "swpic_autotune": (C.c_int, [_CTX, C.c_int32, C.c_char_p]),
     "swpic_set_pipeline": (C.c_int, [_CTX, C.c_int32]),
     "swpic_get_pipeline": (C.c_int, [_CTX, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
+    "swpic_set_wait_test": (C.c_int, [_CTX, C.c_int32, C.c_int64]),
     "swpic_set_timing": (C.c_int, [_CTX, C.c_int32]),
     "swpic_pass_times": (C.c_int, [_CTX, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
     "swpic_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
@@ -357,6 +359,10 @@ def swpic_get_pipeline(ctx):
     a, b = C.c_int32(), C.c_int32()
     _check(load_library().swpic_get_pipeline(ctx, C.byref(a), C.byref(b)), ctx)
     return a.value, b.value
+
+
+def swpic_set_wait_test(ctx, stall_warp=-1, wait_limit_ns=0):
+    _check(load_library().swpic_set_wait_test(ctx, int(stall_warp), int(wait_limit_ns)), ctx)
 
 
 def swpic_set_timing(ctx, enable):

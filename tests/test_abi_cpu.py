@@ -63,7 +63,7 @@ int main(void) {
   printf("%zu %zu %zu\\n", sizeof(swpic_config), sizeof(swpic_diag), sizeof(swpic_lattice));
   printf("%zu %zu %zu\\n", offsetof(swpic_config, diag_capacity), offsetof(swpic_diag, step),
          offsetof(swpic_lattice, decorate));
-  printf("%d %d\\n", SWPIC_ABI_VERSION, SWPIC_NX_MAX);
+  printf("%d %d %d\\n", SWPIC_ABI_VERSION, SWPIC_NX_MAX, SWPIC_STATIC_NX_MAX);
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -76,7 +76,7 @@ int main(void) {
                      C.sizeof(swpic.swpic_lattice)]
     assert offs == [swpic.swpic_config.diag_capacity.offset, swpic.swpic_diag.step.offset,
                     swpic.swpic_lattice.decorate.offset]
-    assert [int(x) for x in lines[2].split()] == [1, swpic.SWPIC_NX_MAX]
+    assert [int(x) for x in lines[2].split()] == [1, swpic.SWPIC_NX_MAX, swpic.SWPIC_STATIC_NX_MAX]
 
 
 def test_status_strings_and_version_without_gpu(lib):

@@ -357,6 +357,19 @@ def test_checkpoint_resume(tmp_path):
     _compare(got, ref, Lx, Ly, 1e-12)
     np.testing.assert_array_equal(dgot[:, 8], np.arange(4, 8))
     assert rel_max(dgot[:, 6], dref[-4:, 6]) < 1e-12
+    # a context that has already stepped loads the same file: its earlier
+    # records are discarded and the records restart at the checkpoint
+    d = _sim(Lx, Ly, nx, ny, dt, 2500, 64)
+    try:
+        d.init_particles(st)
+        d.step(6, 1)
+        swpic.swpic2d_load(d.ctx, path)
+        d.step(4, 1)
+        got2, dgot2 = d.state(), d.diagnostics()
+    finally:
+        d.close()
+    _compare(got2, ref, Lx, Ly, 1e-12)
+    np.testing.assert_array_equal(dgot2[:, 8], np.arange(4, 8))
     c = _sim(Lx, Ly, nx, ny, dt, 2500, 32)
     try:
         with pytest.raises(swpic.SwpicError) as e:

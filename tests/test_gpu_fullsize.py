@@ -5,7 +5,8 @@ Each side initialises from the same lattice description (the device with
 its own kernel, the oracle with its own code), takes one step, and the
 mesh charge and sampled particles are compared.  The FP32 comparisons use
 the oracle's FP32-storage mode (element decisions from FP32-stored
-positions, FP64 arithmetic).
+positions, FP64 arithmetic); the bump-on-tail step is also compared with the
+plain FP64 oracle.
 """
 import numpy as np
 import pytest
@@ -60,6 +61,11 @@ def test_bump_on_tail_full_size_one_fp32_step():
                   elem=O.element_key(ref["Q"], lat.L, spec.nx, np.float32))
     assert rel_max(m["b"], b) <= 1e-5
     _check_sample(got, ref, idx, lat.L, 1e-6)
+    # the same step against the plain FP64 oracle (FP64 state and element
+    # decisions from the same initial values): mesh charge within 1e-5
+    ref64 = O.run(st, spec.nx, lat.L, spec.dt, 1, diag_every=0)
+    f64 = O.field_of_state(ref64["Q"], ref64["ps"], ref64["psi"], lat.L, spec.nx)
+    assert rel_max(m["b"], f64["b"]) <= 1e-5
 
 
 def test_strong_landau_full_size_one_fp64_step():

@@ -227,9 +227,16 @@ def test_gather_push_matches_oracle(prec, d2_mode):
         sl = slice(off, off + n)
         s = {k: st0[k][sl].copy() for k in st0}
         elem = O.element_key(s["Q"], L, nx, dt_)
-        # field tables exactly as the device holds them (rounded to storage precision)
-        dphi = (-meshes[r]["E"]).astype(dt_).astype(np.float64)
-        d2 = meshes[r]["d2"]
+        # the oracle's own field of the same stored state (Eq. rhs-assembly with
+        # the elements decided in the state's precision, the Galerkin solve, the
+        # tables), rounded to the storage precision of the step's tables
+        b = O.deposit(s["Q"], s["ps"], s["psi"], L, nx, elem=elem)
+        Phi, lam = O.solve(b, L)
+        dphi, d2 = O.field_tables(Phi, L, d2_mode, btilde=b - lam)
+        dphi = dphi.astype(dt_).astype(np.float64)
+        d2 = d2.astype(dt_).astype(np.float64)
+        # the FP32 deposit forms its node weights in FP32 (the deposit tolerance)
+        assert rel_max(-meshes[r]["E"], dphi) <= (1e-5 if prec == 32 else 1e-12)
         dV, d2V = O.gather(s["Q"], L, dphi, d2, d2_mode=d2_mode, elem=elem)
         O.kick_values(s["ps"], s["P"], s["qs"], dV, d2V, 0.5 * dt)
         O.drift(s["Q"], s["P"], s["qs"], s["ps"], L, dt)

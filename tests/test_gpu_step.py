@@ -116,6 +116,45 @@ def test_one_fp32_step_mesh_charge_within_1e5(mode):
     _compare_state(got, ref, lat.L, 1e-6)
 
 
+def _node_dipole_allowance(Q, ps, L, nx):
+    """Sum of 2|p*|/h over the particles within 4 FP32 ulps of a node: the
+    element decision of such a particle may differ between an FP32 state and
+    an FP64 state, and the dipole term -p* phi_j'(Q) of Eq. rhs-assembly
+    jumps by 2 p*/h across a node (the monopole term is continuous)."""
+    x = np.asarray(Q, dtype=np.float64) * (nx / L)
+    d = np.abs(x - np.round(x))
+    ulp = np.spacing(np.float32(L)).astype(np.float64) * (nx / L)
+    near = d <= 4 * ulp
+    return float(np.sum(2 * np.abs(ps[near])) * nx / L)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_one_fp32_step_mesh_charge_vs_plain_fp64_oracle(mode):
+    """The same FP32 step against the plain FP64 oracle (FP64 state, FP64
+    element decisions), from the same FP32-representable initial values: the
+    mesh charge agrees within 1e-5 relative, plus the dipole jump of the
+    particles that sit within FP32 rounding of a node (their element may be
+    decided differently; one such particle of this jittered lattice moves
+    ~1e-4 of max |b|)."""
+    need_gpu()
+    lat = W.LatticeSpec(512, 256, 4 * np.pi, -6.0, 6.0, 0.5, 0.5, W.MAXWELL, jitter=0.25, seed=0)
+    jx, jv = W.jitter(lat)
+    st = cast_state(O.init_lattice(lat, jx, jv), 32)
+    nx, dt = 128, 0.05
+    sim = _sim([(lat.L, dt, nx, lat.n)], 32, deposit_mode=mode)
+    try:
+        sim.init_particles(st)
+        sim.step(1)
+        m = sim.mesh(0)
+    finally:
+        sim.close()
+    ref = O.run(st, nx, lat.L, dt, 1, diag_every=0)
+    f = O.field_of_state(ref["Q"], ref["ps"], ref["psi"], lat.L, nx)
+    scale = np.abs(f["b"]).max()
+    allow = _node_dipole_allowance(ref["Q"], ref["ps"], lat.L, nx)
+    assert np.abs(m["b"] - f["b"]).max() <= 1e-5 * scale + allow, (rel_max(m["b"], f["b"]), allow / scale)
+
+
 def test_step_in_pieces_equals_fused_step():
     """KDK = gather_push(1/2, 1); deposit; solve_field; gather_push(1/2, 0)."""
     need_gpu()

@@ -546,6 +546,22 @@ def test_strong_landau_paper_setup_damping_rate():
         assert abs(rates[0] / rates[1] - 1) < 0.01, (side, rates)
 
 
+def test_two_beam_root_cold_limit_and_the_printed_rate():
+    """The warm two-beam dispersion relation used to read Sec. 7.2: as T -> 0
+    it tends to the cold symmetric-beam relation (w^2 - x^2)^2 = w^2 + x^2
+    (x = k u, n0 = 1), whose growing root is
+    gamma^2 = [sqrt(8 x^2 + 1) - (2 x^2 + 1)]/2; at the printed setup (u = 1,
+    T = 0.09, L = 2 pi so k = 1, n0 = 1) the root is about 0.21, far from the
+    printed 0.7863, which needs n0 of about 20 (gamma 0.78 there)."""
+    for x in (0.4, 0.6, 0.8):
+        cold = math.sqrt((math.sqrt(8 * x * x + 1) - (2 * x * x + 1)) / 2)
+        warm = ph.two_beam_root(x, T=1e-5)
+        assert abs(warm / cold - 1) < 0.01, (x, warm, cold)
+    g1 = ph.two_beam_root(1.0, n0=1.0)
+    assert 0.19 < g1 < 0.22
+    assert abs(ph.two_beam_root(1.0, n0=20.0) / 0.7863 - 1) < 0.02
+
+
 def test_wrap_maps_round_up_into_domain():
     """Reading A5: a position that rounds up to exactly L wraps to 0."""
     L = 4 * math.pi

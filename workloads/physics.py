@@ -67,6 +67,29 @@ def bump_on_tail_root(k, guess=1.0 + 0.2j):
     return _solve(eps, guess)
 
 
+def two_beam_root(k, n0=1.0, u=1.0, T=0.09, guesses=(0.1, 0.3, 0.6, 0.9, 1.2, 1.5)):
+    """Fastest purely growing root of two Maxwellian beams at +-u, temperature
+    T, each of density n0/2 (the warm two-stream setup of Sec. 7.2):
+    eps = 1 + sum_b (n0/2)(1 + zeta_b Z(zeta_b))/(T k^2), zeta_b = (w/k -+ u)/sqrt(2T).
+    Returns the growth rate (0 when no growing root is found)."""
+    def eps(w):
+        tot = 0
+        for ub in (u, -u):
+            z = (w / k - ub) / math.sqrt(2 * T)
+            tot += 0.5 * n0 / T * (1 + z * Zfun(z))
+        return 1 + tot / k ** 2
+    best = 0.0
+    for g0 in guesses:
+        try:
+            with np.errstate(all="ignore"):
+                r = _solve(eps, complex(0.0, g0))
+        except Exception:
+            continue
+        if abs(eps(r)) < 1e-8 and abs(r.real) < 1e-6 and r.imag > best:
+            best = r.imag
+    return best
+
+
 def rate_fit(t, E, t0, t1, min_sep=None):
     """Least-squares slope of log E at local maxima inside [t0, t1].
     Maxima closer than ``min_sep`` are merged (the larger kept).  The
