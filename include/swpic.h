@@ -90,7 +90,8 @@ typedef struct swpic_config {
     int32_t deposit_mode;      /* swpic_deposit_mode                             */
     int32_t d2_mode;           /* swpic_d2_mode                                  */
     int32_t resort_every;      /* stable sort by cell every K steps; 0 = never   */
-    int32_t threads_per_block; /* 0 = default (256); 64..1024, multiple of 32    */
+    int32_t threads_per_block; /* 0 = default (256); a multiple of 32 in 64..768
+                                  (FP32 state) or 64..512 (FP64 state)           */
     int32_t blocks_per_sm;     /* 0 = default (3 FP32, 2 FP64)                   */
     int32_t use_graphs;        /* 1 = capture swpic_step() in CUDA graphs        */
     int32_t diag_capacity;     /* diagnostic records kept per run (0 = 4096)     */
@@ -360,8 +361,9 @@ swpic_status swpic_get_launch(const swpic_ctx *ctx, int32_t *threads_per_block,
 swpic_status swpic_set_pipeline(swpic_ctx *ctx, int32_t stages);
 swpic_status swpic_get_pipeline(const swpic_ctx *ctx, int32_t *requested, int32_t *effective);
 
-/* Times a small grid of launch shapes, particle-load pipelines and re-sort
- * intervals on the bound state (which is saved before and restored after, bit
+/* Times a small grid of launch shapes (threads per block 128, 192, 256, 384,
+ * 512, 768 up to the precision's limit, x CTAs per SM 1..8 within 2048
+ * threads), particle-load pipelines and re-sort intervals on the bound state (which is saved before and restored after, bit
  * for bit; trial steps record diagnostics every step) and keeps the fastest.
  * Tune on a state like the one to be run: the fastest shape for a freshly
  * initialised (ordered) lattice differs from the one for a mixed plasma.

@@ -110,6 +110,10 @@ swpic_status fail_cuda(swpic_ctx *ctx, const char *what, cudaError_t e) {
     } while (0)
 
 size_t elem_size(int prec) { return prec == SWPIC_F64 ? 8 : 4; }
+// largest CTA of the particle pass: the FP32 pass is held to 80 registers a
+// thread (768 x 80 = 61,440 of the SM's 65,536), the FP64 pass is compiled for
+// at most 512 threads
+int max_tpb(int prec) { return prec == SWPIC_F64 ? 512 : 768; }
 int vec_width(int prec) { return prec == SWPIC_F64 ? 2 : 4; }
 int64_t seg_bytes(int64_t n, int prec) { return (n * (int64_t)elem_size(prec) + 255) / 256 * 256; }
 
@@ -153,8 +157,9 @@ swpic_status validate_cfg(const swpic_config &c, std::string &why) {
     }
     if (c.resort_every < 0) { why = "resort_every must be >= 0"; return SWPIC_EINVAL; }
     if (c.threads_per_block != 0 &&
-        (c.threads_per_block < 64 || c.threads_per_block > 512 || c.threads_per_block % 32)) {
-        why = "threads_per_block must be 0 or a multiple of 32 in [64, 512]"; return SWPIC_EINVAL;
+        (c.threads_per_block < 64 || c.threads_per_block > max_tpb(c.precision) || c.threads_per_block % 32)) {
+        why = "threads_per_block must be 0 or a multiple of 32 in [64, 768] (FP32) or [64, 512] (FP64)";
+        return SWPIC_EINVAL;
     }
     if (c.blocks_per_sm < 0 || c.blocks_per_sm > 32) { why = "blocks_per_sm must be in [0, 32]"; return SWPIC_EINVAL; }
     if (c.diag_capacity < 0) { why = "diag_capacity must be >= 0"; return SWPIC_EINVAL; }
@@ -1045,7 +1050,8 @@ swpic_status swpic_load(swpic_ctx *ctx, const char *path) {
 // ---- launch shape, tuning, measurement ----------------------------------------
 swpic_status swpic_set_launch(swpic_ctx *ctx, int32_t tpb, int32_t bpsm, int32_t resort) {
     if (!ctx) return SWPIC_EINVAL;
-    if (tpb != 0 && (tpb < 64 || tpb > 512 || tpb % 32)) return fail(ctx, SWPIC_EINVAL, "bad threads_per_block");
+    if (tpb != 0 && (tpb < 64 || tpb > max_tpb(ctx->prec) || tpb % 32))
+        return fail(ctx, SWPIC_EINVAL, "bad threads_per_block");
     if (bpsm < 0 || bpsm > 32) return fail(ctx, SWPIC_EINVAL, "bad blocks_per_sm");
     if (resort < 0) return fail(ctx, SWPIC_EINVAL, "bad resort_every");
     if (tpb) ctx->tpb = tpb;
@@ -1174,7 +1180,7 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    const int tpbs[] = {128, 256, 512};
+    const int tpbs[] = {128, 192, 256, 384, 512, 768};
     const int bpsms[] = {1, 2, 3, 4, 6, 8};
     std::vector<int> rss = {0};
     if (ctx->scratch) { rss.push_back(5); rss.push_back(20); rss.push_back(50); }
@@ -1183,6 +1189,7 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
     int bt = tpb0, bb = bpsm0, br = rs0, bp = pipe0;
     swpic_status st = SWPIC_OK;
     for (int tpb : tpbs) {
+        if (tpb > max_tpb(ctx->prec)) continue;
         for (int bpsm : bpsms) {
             if (tpb * bpsm > 2048) continue;
             for (int pipe : pipes) {

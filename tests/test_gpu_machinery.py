@@ -88,7 +88,8 @@ def test_autotune_restores_state_and_picks_a_valid_shape(tmp_path):
         assert sim.diagnostics().shape[0] == nrec0
         tpb, bpsm, resort = swpic.swpic_get_launch(sim.ctx)
         req, eff = swpic.swpic_get_pipeline(sim.ctx)
-        assert tpb in (128, 256, 512) and bpsm in (1, 2, 3, 4, 6, 8) and resort in (0, 5, 20, 50)
+        assert tpb in (128, 192, 256, 384, 512, 768) and bpsm in (1, 2, 3, 4, 6, 8)
+        assert tpb * bpsm <= 2048 and resort in (0, 5, 20, 50)
         assert eff == 0 or 2 <= eff <= req
         with open(cache) as f:
             entries = json.load(f)
