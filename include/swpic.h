@@ -363,7 +363,10 @@ swpic_status swpic_get_pipeline(const swpic_ctx *ctx, int32_t *requested, int32_
 
 /* Times a small grid of launch shapes (threads per block 128, 192, 256, 384,
  * 512, 768 up to the precision's limit, x CTAs per SM 1..8 within 2048
- * threads), particle-load pipelines and re-sort intervals on the bound state (which is saved before and restored after, bit
+ * threads), particle-load pipelines and re-sort intervals on the bound state,
+ * then, for the best shape with the bulk-copy stream, 2, 3 and 4 stages with
+ * and without issuing each CTA's first copies before it stages its field
+ * table (which is saved before and restored after, bit
  * for bit; trial steps record diagnostics every step) and keeps the fastest.
  * Tune on a state like the one to be run: the fastest shape for a freshly
  * initialised (ordered) lattice differs from the one for a mixed plasma.

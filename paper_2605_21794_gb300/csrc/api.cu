@@ -89,6 +89,7 @@ struct swpic_ctx {
     bool timing = false;
     unsigned long long wait_limit_ns = 1000000000ull;   // 1 s
     int32_t stall_warp = -1;
+    int prefetch = 1;                 // first bulk copies before the table staging (autotuned)
     std::vector<cudaEvent_t> events;
     int n_timed = 0;
     int64_t launches = 0;
@@ -211,6 +212,7 @@ PassArgs base_args(swpic_ctx *ctx) {
     a.err = ctx->d_err;
     a.wait_limit_ns = ctx->wait_limit_ns;
     a.stall_warp = ctx->stall_warp;
+    a.prefetch = ctx->prefetch;
     return a;
 }
 
@@ -1145,6 +1147,9 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
             const char *g = std::strstr(p, "\"pipeline_stages\":");
             if (a && b && c && g && std::sscanf(a + 20, "%d", &tpb) == 1 && std::sscanf(b + 16, "%d", &bpsm) == 1 &&
                 std::sscanf(c + 15, "%d", &rs) == 1 && std::sscanf(g + 18, "%d", &stg) == 1) {
+                const char *h = std::strstr(p, "\"prefetch\":");
+                int pf = 1;
+                if (h && std::sscanf(h + 11, "%d", &pf) == 1) ctx->prefetch = pf ? 1 : 0;
                 swpic_status q = swpic_set_pipeline(ctx, stg);
                 return q != SWPIC_OK ? q : swpic_set_launch(ctx, tpb, bpsm, rs);
             }
@@ -1186,8 +1191,23 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
     if (ctx->scratch) { rss.push_back(5); rss.push_back(20); rss.push_back(50); }
     const int pipes[] = {0, kDefaultStages};
     float best = 1e30f;
-    int bt = tpb0, bb = bpsm0, br = rs0, bp = pipe0;
+    int bt = tpb0, bb = bpsm0, br = rs0, bp = pipe0, bf = ctx->prefetch;
     swpic_status st = SWPIC_OK;
+    // time per step of n_trial steps from the snapshot with the current settings (best of two)
+    auto trial = [&](int n_trial) -> float {
+        float ms = 0.f, lo = 1e30f;
+        for (int rep = 0; rep < 2 && st == SWPIC_OK; ++rep) {
+            st = restore();
+            if (st != SWPIC_OK) break;
+            cudaEventRecord(e0, ctx->stream);
+            st = swpic_step(ctx, n_trial, 1);      // steps with their diagnostics
+            cudaEventRecord(e1, ctx->stream);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, SWPIC_ECUDA, "autotune trial");
+            cudaEventElapsedTime(&ms, e0, e1);
+            lo = std::min(lo, ms);
+        }
+        return lo / (float)n_trial;
+    };
     for (int tpb : tpbs) {
         if (tpb > max_tpb(ctx->prec)) continue;
         for (int bpsm : bpsms) {
@@ -1201,18 +1221,8 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
                     // a trial covers at least two re-sort intervals so the sort cost is
                     // amortised as in a long run; the score is time per step
                     const int n_trial = std::max(steps_per_trial, rs > 0 ? 2 * rs : 0);
-                    float ms = 0.f;
-                    for (int rep = 0; rep < 2 && st == SWPIC_OK; ++rep) {
-                        st = restore();
-                        if (st != SWPIC_OK) break;
-                        cudaEventRecord(e0, ctx->stream);
-                        st = swpic_step(ctx, n_trial, 1);      // steps with their diagnostics
-                        cudaEventRecord(e1, ctx->stream);
-                        if (cudaEventSynchronize(e1) != cudaSuccess) st = fail(ctx, SWPIC_ECUDA, "autotune trial");
-                        cudaEventElapsedTime(&ms, e0, e1);
-                    }
+                    const float ms = trial(n_trial);
                     if (st != SWPIC_OK) break;
-                    ms /= (float)n_trial;
                     if (ms < best) { best = ms; bt = tpb; bb = bpsm; br = rs; bp = pipe; }
                 }
                 if (st != SWPIC_OK) break;
@@ -1221,9 +1231,27 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
         }
         if (st != SWPIC_OK) break;
     }
+    // refine the bulk-copy stream of the best shape: stage count, and whether a
+    // CTA issues its first copies before it stages its table
+    if (st == SWPIC_OK && bp > 0) {
+        ctx->tpb = bt; ctx->bpsm = bb; ctx->resort = br;
+        const int n_trial = std::max(steps_per_trial, br > 0 ? 2 * br : 0);
+        for (int pipe : {2, 3, 4}) {
+            ctx->pipe = pipe;
+            if (pass_stages(ctx) != pipe) continue;            // this stage count does not fit
+            for (int pf : {1, 0}) {
+                ctx->prefetch = pf;
+                clear_graphs(ctx);
+                const float ms = trial(n_trial);
+                if (st != SWPIC_OK) break;
+                if (ms < best) { best = ms; bp = pipe; bf = pf; }
+            }
+            if (st != SWPIC_OK) break;
+        }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    ctx->tpb = bt; ctx->bpsm = bb; ctx->resort = br; ctx->pipe = bp;
+    ctx->tpb = bt; ctx->bpsm = bb; ctx->resort = br; ctx->pipe = bp; ctx->prefetch = bf;
     clear_graphs(ctx);
     swpic_status rs_ = restore();
     for (void *p : snap) if (p) cudaFree(p);
@@ -1233,8 +1261,8 @@ swpic_status swpic_autotune(swpic_ctx *ctx, int32_t steps_per_trial, const char 
         char line[768];
         std::snprintf(line, sizeof(line),
                       " \"%s\": {\"threads_per_block\": %d, \"blocks_per_sm\": %d, \"resort_every\": %d, "
-                      "\"pipeline_stages\": %d, \"ms_per_step\": %.6g}",
-                      key, bt, bb, br, bp, best);
+                      "\"pipeline_stages\": %d, \"prefetch\": %d, \"ms_per_step\": %.6g}",
+                      key, bt, bb, br, bp, bf, best);
         std::string body;
         const size_t open = text.find('{'), close = text.rfind('}');
         if (open != std::string::npos && close != std::string::npos && close > open) {

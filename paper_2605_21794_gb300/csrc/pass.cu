@@ -1081,12 +1081,13 @@ struct Pipe {
     uint64_t *bar;           // this warp's S mbarriers
     int S;
     uint32_t seq;
+    int pre;                 // turns of the next segment already issued (prefetched)
 };
 
 template <typename T, bool DEC, int MODE, bool DEP, bool DIAG, int D2>
 __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t s, int64_t e,
                                      const typename Vec2<T>::type *s_tab, void *s_mesh, void *s_mesh_m, Thread<T> &th,
-                                     int32_t *err, Pipe &pp, int *s_abort) {
+                                     int32_t *err, Pipe &pp, int *s_abort, bool prefetch_only = false) {
     using V = typename Vec16<T>::type;
     constexpr int VW = Vec16<T>::n;
     constexpr int NA = DEC ? 5 : 3;                       // Q, P, w [, q*, p*]
@@ -1125,10 +1126,12 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
     const int64_t vs = (s + A - 1) / A * A;
     const int64_t ve = e / A * A;
     if (vs >= ve) {
+        if (prefetch_only) return true;
         for (int64_t k = s + threadIdx.x; k < e; k += blockDim.x) scalar(k);
         return true;
     }
-    for (int64_t k = s + threadIdx.x; k < vs; k += blockDim.x) scalar(k);
+    if (!prefetch_only)
+        for (int64_t k = s + threadIdx.x; k < vs; k += blockDim.x) scalar(k);
 
     const int64_t v0 = vs / VW, v1 = ve / VW;
     const int lane = threadIdx.x & 31;
@@ -1155,8 +1158,17 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
         for (int j = 0; j < NA; ++j) bulk_load(st + j * ARR, reinterpret_cast<const V *>(src[j]) + gv, nb, bar);
     };
 
+    if (prefetch_only) {
+        // the first turns only, issued before the CTA stages its table and
+        // clears its mesh, so their latency overlaps that work
+        if (lane == 0)
+            for (int k = 0; k < S && k < nturn; ++k) issue(k);
+        pp.pre = min(S, nturn);
+        return true;
+    }
     if (lane == 0)
-        for (int k = 0; k < S && k < nturn; ++k) issue(k);
+        for (int k = pp.pre; k < S && k < nturn; ++k) issue(k);
+    pp.pre = 0;
     int issued = min(S, nturn);
     bool ok = true;
     int k = 0;
@@ -1264,6 +1276,7 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
         constexpr size_t stage_bytes = (DEC ? 5 : 3) * TurnVecs<T>::n * sizeof(typename Vec16<T>::type);
         pp.S = a.stages;
         pp.seq = 0;
+        pp.pre = 0;
         pp.bar = reinterpret_cast<uint64_t *>(smem + bar_offset(tb, mb)) + (size_t)w * pp.S;
         pp.base = smem + stage_area_offset(tb, mb, nw, pp.S) + (size_t)w * pp.S * stage_bytes;
     }
@@ -1284,6 +1297,19 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
     int r = find_run(a.runs, a.n_runs, c0);
     int64_t pos = c0;
     const bool last_work = (a.flags & (PASS_SOLVE | PASS_DIAG | PASS_COUNT_STEP)) != 0;
+    if (bulk && a.prefetch && r < a.n_runs) {
+        // issue the first segment's first bulk copies now, before the table is
+        // staged and the mesh cleared (see process_segment_bulk)
+        int rr = r;
+        while (rr < a.n_runs && min(c1, a.runs[rr].p1) <= pos) ++rr;
+        if (rr < a.n_runs) {
+            const RunDev R0 = a.runs[rr];
+            const T2 *tab0 = reinterpret_cast<const T2 *>(smem);
+            Thread<T> th0;
+            process_segment_bulk<T, DEC, MODE, DEP, DIAG, D2>(a, R0, pos, min(c1, R0.p1), tab0, s_mesh, s_mesh_m,
+                                                              th0, a.err + rr, pp, &s_abort, true);
+        }
+    }
     while (pos < c1 && r < a.n_runs) {
         const RunDev R = a.runs[r];
         const int64_t s = pos, e = min(c1, R.p1);

@@ -103,6 +103,7 @@ struct PassArgs {
     unsigned long long wait_limit_ns;   // bound of every mbarrier wait of the bulk-copy stream
     int32_t stall_warp;       // test hook: this warp (grid-wide index) never arms its first
                               // stage, so its first wait runs out; -1 = none
+    int32_t prefetch;         // 1: issue a CTA's first bulk copies before it stages its table
 };
 
 // shared-memory bytes of the pass kernel / the per-run solve for a given max nx
