@@ -740,8 +740,15 @@ __device__ __forceinline__ void push_vector_f2(float2 &q, float2 &p, float2 &x, 
     f2p FI;
     elem2(mul2(Q, INVH), G.cmax, i0, i1, FI);
     const float2 t0 = s_tab[i0], t1 = s_tab[i1];
-    const f2p D1 = pk2(t0.x, t1.x);
+    f2p D1 = pk2(t0.x, t1.x);
     f2p D2v = pk2(t0.y, t1.y);
+    if (D2 == SWPIC_D2_P2) {
+        // P2: phi_h' = a + beta (1 - 2 xi) and phi_h'' = -2 beta / h on the element
+        const f2p XI = fma2(Q, splat2(G.inv_h_lo), fma2(Q, INVH, sub2(splat2(0.0f), FI)));
+        const f2p BETA = D2v;
+        D1 = fma2(BETA, sub2(splat2(1.0f), mul2(splat2(2.0f), XI)), D1);
+        if (DEC) D2v = mul2(splat2(-2.0f * G.inv_h), BETA);
+    }
     if (DEC && D2 == SWPIC_D2_NODAL) {
         // xi = Q nx/L - i with the low part of nx/L added back; phi'' linear in xi
         const f2p XI = fma2(Q, splat2(G.inv_h_lo), fma2(Q, INVH, sub2(splat2(0.0f), FI)));
@@ -801,6 +808,13 @@ __device__ __forceinline__ void push_vector_f2(float2 &q, float2 &p, float2 &x, 
         }
         upk2(W0, o.w0[0], o.w0[1]);
         upk2(W1, o.w1[0], o.w1[1]);
+        if (D2 == SWPIC_D2_P2) {
+            // the midpoint load psi* N_m(xi) - p* N_m'(xi), N_m = 4 xi (1 - xi)
+            f2p WM = mul2(mul2(mul2(splat2(4.0f), W), XI), sub2(splat2(1.0f), XI));
+            if (DEC)
+                WM = fma2(mul2(sub2(splat2(0.0f), PS), INVH), sub2(splat2(4.0f), mul2(splat2(8.0f), XI)), WM);
+            upk2(WM, o.wm[0], o.wm[1]);
+        }
     }
     upk2(Q, q.x, q.y);
     upk2(P, p.x, p.y);
@@ -818,8 +832,8 @@ __device__ __forceinline__ void push_vector(typename Vec16<T>::type &q, typename
                                             const typename Vec16<T>::type &m,
                                             const typename Vec2<T>::type *s_tab, int nx, const Geo<T> &G,
                                             T k1, T k2, T kd, Thread<T> &th, VecOut<T> &o) {
-    if constexpr (sizeof(T) == 4 && D2 != SWPIC_D2_P2) {
-        // FP32 P1 field: both particles of the vector in packed arithmetic
+    if constexpr (sizeof(T) == 4) {
+        // FP32: both particles of the vector in packed arithmetic
         push_vector_f2<DEC, DEP, DIAG, D2>(q, p, x, y, m, s_tab, nx, G, k1, k2, kd, th, o);
         return;
     }
