@@ -922,6 +922,11 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
     step_coefficients(a, R, k1, k2, kd);
     const T scale = opaque((T)R.fx_scale);      // a power of two: exact in either type
     const bool wpsi = (a.flags & PASS_WRITE_PSI) != 0;
+    // a half-kick without drift (the closing half-kick of a step) leaves Q and
+    // p* as they are and does not write them back; a pass from the sort buffer
+    // writes every array, and a pass with neither kick nor drift (the field of
+    // a refreshed state) stores the wrapped positions
+    const bool wdrift = a.cd != 0.0 || wpsi || (a.c1 == 0.0 && a.c2 == 0.0);
     const T *Qi = reinterpret_cast<const T *>(a.Qi), *Pi = reinterpret_cast<const T *>(a.Pi);
     const T *qsi = reinterpret_cast<const T *>(a.qsi), *psi = reinterpret_cast<const T *>(a.psi_i);
     const T *wi = reinterpret_cast<const T *>(a.wi);
@@ -938,9 +943,12 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
         T w0 = T(0), w1 = T(0), wm = T(0), dm = T(0), dk = T(0);
         push_one<T, DEC, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, dm, dk, key, w0, w1, wm);
         if (DIAG) { th.mom.add(dm); th.kin.add(dk); }
-        Qo[k] = Q;
+        if (wdrift) Qo[k] = Q;
         Po[k] = P;
-        if (DEC) { qso[k] = qs; pso[k] = ps; }
+        if (DEC) {
+            qso[k] = qs;
+            if (wdrift) pso[k] = ps;
+        }
         if (wpsi) wo[k] = w;
         if (DEP) mesh_add<T, MODE>(key, w0, w1, s_mesh, scale, err);
         if (DEP && D2 == SWPIC_D2_P2) mesh_m_add<T, MODE>(key, wm, s_mesh_m, scale, err);
@@ -988,11 +996,11 @@ __device__ void process_segment(const PassArgs &a, const RunDev &R, int64_t s, i
         if (cur_ok) {
             push_vector<T, DEC, DEP, DIAG, D2>(cur.q, cur.p, cur.x, cur.y, cur.m, s_tab, nx, G, k1, k2, kd, th, o);
             const int64_t vv = vec_of(t);
-            reinterpret_cast<V *>(Qo)[vv] = cur.q;
+            if (wdrift) reinterpret_cast<V *>(Qo)[vv] = cur.q;
             reinterpret_cast<V *>(Po)[vv] = cur.p;
             if (DEC) {
                 reinterpret_cast<V *>(qso)[vv] = cur.x;
-                reinterpret_cast<V *>(pso)[vv] = cur.y;
+                if (wdrift) reinterpret_cast<V *>(pso)[vv] = cur.y;
             }
             if (wpsi) reinterpret_cast<V *>(wo)[vv] = cur.m;
         } else {
@@ -1113,6 +1121,11 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
     step_coefficients(a, R, k1, k2, kd);
     const T scale = opaque((T)R.fx_scale);      // a power of two: exact in either type
     const bool wpsi = (a.flags & PASS_WRITE_PSI) != 0;
+    // a half-kick without drift (the closing half-kick of a step) leaves Q and
+    // p* as they are and does not write them back; a pass from the sort buffer
+    // writes every array, and a pass with neither kick nor drift (the field of
+    // a refreshed state) stores the wrapped positions
+    const bool wdrift = a.cd != 0.0 || wpsi || (a.c1 == 0.0 && a.c2 == 0.0);
     const T *Qi = reinterpret_cast<const T *>(a.Qi), *Pi = reinterpret_cast<const T *>(a.Pi);
     const T *qsi = reinterpret_cast<const T *>(a.qsi), *psi = reinterpret_cast<const T *>(a.psi_i);
     const T *wi = reinterpret_cast<const T *>(a.wi);
@@ -1128,9 +1141,12 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
         T w0 = T(0), w1 = T(0), wm = T(0), dm = T(0), dk = T(0);
         push_one<T, DEC, DEP, DIAG, D2>(Q, P, qs, ps, w, s_tab, nx, G, k1, k2, kd, dm, dk, key, w0, w1, wm);
         if (DIAG) { th.mom.add(dm); th.kin.add(dk); }
-        Qo[k] = Q;
+        if (wdrift) Qo[k] = Q;
         Po[k] = P;
-        if (DEC) { qso[k] = qs; pso[k] = ps; }
+        if (DEC) {
+            qso[k] = qs;
+            if (wdrift) pso[k] = ps;
+        }
         if (wpsi) wo[k] = w;
         if (DEP) mesh_add<T, MODE>(key, w0, w1, s_mesh, scale, err);
         if (DEP && D2 == SWPIC_D2_P2) mesh_m_add<T, MODE>(key, wm, s_mesh_m, scale, err);
@@ -1230,11 +1246,11 @@ __device__ bool process_segment_bulk(const PassArgs &a, const RunDev &R, int64_t
         for (int u = 0; u < U; ++u) {
             if (have[u]) {
                 const int64_t vv = wbase + (int64_t)k * stride + 32 * u + lane;
-                reinterpret_cast<V *>(Qo)[vv] = qv[u];
+                if (wdrift) reinterpret_cast<V *>(Qo)[vv] = qv[u];
                 reinterpret_cast<V *>(Po)[vv] = pv[u];
                 if (DEC) {
                     reinterpret_cast<V *>(qso)[vv] = xv[u];
-                    reinterpret_cast<V *>(pso)[vv] = yv[u];
+                    if (wdrift) reinterpret_cast<V *>(pso)[vv] = yv[u];
                 }
                 if (wpsi) reinterpret_cast<V *>(wo)[vv] = mv[u];
             }
