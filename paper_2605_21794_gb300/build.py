@@ -39,7 +39,8 @@ def build(force=False, verbose=False):
     os.makedirs(OUT_DIR, exist_ok=True)
     nvcc = _nvcc()
     headers = [os.path.join(INCLUDE, "swpic.h"), os.path.join(CSRC, "swpic_internal.cuh"),
-               os.path.join(INCLUDE, "swpic2d.h"), os.path.join(CSRC, "swpic2d_internal.cuh")]
+               os.path.join(INCLUDE, "swpic2d.h"), os.path.join(CSRC, "swpic2d_internal.cuh"),
+               os.path.join(CSRC, "f32x2.cuh")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

@@ -34,6 +34,7 @@
 // and rebuilds the (phi_h', phi_h'') table for the next pass.
 #include <math.h>
 
+#include "f32x2.cuh"
 #include "swpic_internal.cuh"
 
 namespace swpic {
@@ -677,41 +678,7 @@ struct VecOut {
 // FP32 instructions.  min, max and negation have no packed form: the clamps
 // of the element index stay scalar, and negated operands are formed as 0 - x.
 // ---------------------------------------------------------------------------
-typedef unsigned long long f2p;          // two packed floats, low half = first particle
-__device__ __forceinline__ f2p pk2(float a, float b) {
-    f2p r;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-    return r;
-}
-__device__ __forceinline__ void upk2(f2p r, float &a, float &b) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ f2p fma2(f2p a, f2p b, f2p c) {
-    f2p d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f2p mul2(f2p a, f2p b) {
-    f2p d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2p add2(f2p a, f2p b) {
-    f2p d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2p sub2(f2p a, f2p b) {
-    f2p d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2p add2_rd(f2p a, f2p b) {
-    f2p d;
-    asm("add.rm.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f2p splat2(float a) { return pk2(a, a); }
+using namespace f32x2;
 
 // element index of both halves of p = Q nx/L (see elem_index_c): clamp,
 // 2^23 + p rounded down, bit pattern minus that of 2^23; fi = floor(p) as floats
