@@ -361,6 +361,29 @@ swpic_status swpic_get_launch(const swpic_ctx *ctx, int32_t *threads_per_block,
 swpic_status swpic_set_pipeline(swpic_ctx *ctx, int32_t stages);
 swpic_status swpic_get_pipeline(const swpic_ctx *ctx, int32_t *requested, int32_t *effective);
 
+/* Where swpic_step solves the field of each deposit (Eq. swpic_poisson; no
+ * counterpart in the paper, a property of this implementation):
+ * LAST_CTA: the CTA that finishes a run's last particles of the depositing
+ *           pass solves it at the end of that pass and writes the run's table.
+ * AT_START: the depositing pass only deposits; every CTA of the next pass
+ *           solves the field of the finished deposit into its own shared-memory
+ *           table at its start, while its first particle copies are in flight,
+ *           and the CTA holding the run's first particle also writes the run's
+ *           table, snapshot, W, E_amp and gauge to global memory.  No pass ends
+ *           in a one-CTA solve.  Each CTA solves once per run it touches.
+ * AUTO (default): AT_START for batches of at most 4 runs, LAST_CTA otherwise.
+ * Both give bitwise the same fields, states and records (the solve is exact
+ * integer arithmetic followed by the same roundings).  The charge
+ * accumulators rotate over three buffers per run.  Invalidates captured
+ * graphs.  EINVAL for any other mode. */
+typedef enum swpic_field_solve {
+    SWPIC_FIELD_SOLVE_AUTO = 0,
+    SWPIC_FIELD_SOLVE_LAST_CTA = 1,
+    SWPIC_FIELD_SOLVE_AT_START = 2
+} swpic_field_solve;
+swpic_status swpic_set_field_solve(swpic_ctx *ctx, int32_t mode);
+swpic_status swpic_get_field_solve(const swpic_ctx *ctx, int32_t *mode, int32_t *effective);
+
 /* Times a small grid of launch shapes (threads per block 128, 192, 256, 384,
  * 512, 768 up to the precision's limit, x CTAs per SM 1..8 within 2048
  * threads), particle-load pipelines and re-sort intervals on the bound state,

@@ -26,11 +26,17 @@ constexpr int kFixedBits = 58;
 constexpr uint32_t PASS_NO_WRITE = 1u << 10;   // host-only marker (never sent to the device)
 constexpr int kDefaultStages = 4;
 constexpr size_t kPassStaticSmem = 2048;       // the pass kernel's static shared memory (~1.4 KB), rounded up
+// automatic field placement: solved at the start of the next pass (by every
+// CTA, once per run it touches) for up to this many runs; batches of more
+// runs keep the one-CTA solve of each run at the end of the depositing pass
+constexpr int kFieldAtStartMaxRuns = 4;
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int64_t kernels = 0;
     int n_passes = 0;
+    int acc_cur_after = 0;        // accumulator rotation and pending field after a replay
+    bool field_pending_after = false;
 };
 
 }  // namespace
@@ -57,6 +63,16 @@ struct swpic_ctx {
     unsigned long long *d_acc = nullptr, *d_done = nullptr;
     long long *d_snap = nullptr, *d_gauge = nullptr;
     unsigned long long *d_acc_m = nullptr;     // P2 element-midpoint load
+    // The charge accumulators rotate over three buffers of total_mesh words
+    // (d_acc and d_acc_m alike): buffer acc_cur holds the deposit of the
+    // current positions, buffer acc_cur + 1 is zero (the next deposit's
+    // target), buffer acc_cur + 2 is cleared by the depositing pass that
+    // makes it the next target.
+    int acc_cur = 0;
+    // the last pass deposited without solving: the next pass solves its field
+    // from buffer acc_cur at its start (PASS_FIELD_ACC)
+    bool field_pending = false;
+    int field_solve = SWPIC_FIELD_SOLVE_AUTO;
     void *d_table = nullptr;
     double *d_b = nullptr, *d_bt = nullptr, *d_e = nullptr, *d_phi = nullptr;
     double *d_diag_acc = nullptr, *d_field_diag = nullptr, *d_mass = nullptr, *d_mabs = nullptr;
@@ -185,6 +201,29 @@ void clear_graphs(swpic_ctx *ctx) {
     ctx->graph_cache.clear();
 }
 
+// buffer acc_cur + k of the accumulator rotation
+unsigned long long *acc_buf(const swpic_ctx *ctx, int k) {
+    return ctx->d_acc + (size_t)((ctx->acc_cur + k) % 3) * (size_t)ctx->total_mesh;
+}
+unsigned long long *acc_m_buf(const swpic_ctx *ctx, int k) {
+    return ctx->d_acc_m + (size_t)((ctx->acc_cur + k) % 3) * (size_t)ctx->total_mesh;
+}
+// zero all three accumulators (the rotation starts over)
+swpic_status clear_accumulators(swpic_ctx *ctx) {
+    CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(unsigned long long) * 3 * (size_t)ctx->total_mesh, ctx->stream));
+    CK(cudaMemsetAsync(ctx->d_acc_m, 0, sizeof(unsigned long long) * 3 * (size_t)ctx->total_mesh, ctx->stream));
+    ctx->acc_cur = 0;
+    ctx->field_pending = false;
+    return SWPIC_OK;
+}
+// the step's depositing passes leave their field to the next pass (every CTA
+// solves it at its start) instead of ending in a one-CTA solve
+bool field_at_start(const swpic_ctx *ctx) {
+    if (ctx->field_solve == SWPIC_FIELD_SOLVE_AT_START) return true;
+    if (ctx->field_solve == SWPIC_FIELD_SOLVE_LAST_CTA) return false;
+    return ctx->R <= kFieldAtStartMaxRuns;
+}
+
 PassArgs base_args(swpic_ctx *ctx) {
     PassArgs a;
     std::memset(&a, 0, sizeof(a));
@@ -195,10 +234,12 @@ PassArgs base_args(swpic_ctx *ctx) {
     a.d2_mode = ctx->d2;
     a.max_nx = ctx->max_nx;
     a.runs = ctx->d_runs;
-    a.acc = ctx->d_acc;
+    a.acc = acc_buf(ctx, 0);
+    a.acc_src = acc_buf(ctx, 0);
     a.snap = ctx->d_snap;
     a.gauge = ctx->d_gauge;
-    a.acc_m = ctx->d_acc_m;
+    a.acc_m = acc_m_buf(ctx, 0);
+    a.acc_m_src = acc_m_buf(ctx, 0);
     a.table = ctx->d_table;
     a.b = ctx->d_b; a.btilde = ctx->d_bt; a.efield = ctx->d_e;
     a.run_done = ctx->d_done;
@@ -246,12 +287,29 @@ void pass_shape(const swpic_ctx *ctx, int *grid, int64_t *chunk) {
 
 // Enqueue one particle pass.  The no-write variant points the outputs at the
 // inputs, which is harmless: a pass with c1 = c2 = cd = 0 rewrites identical values.
+// One pass.  A depositing pass fills buffer acc_cur + 1 and clears buffer
+// acc_cur + 2, and the rotation advances.  defer (the passes of swpic_step):
+// in field-at-start contexts the pass drops its end-of-pass solve and the
+// next pass solves the field at its start.
 swpic_status enqueue_pass(swpic_ctx *ctx, double c1, double c2, double cd, uint32_t flags,
-                          bool from_scratch) {
+                          bool from_scratch, bool defer = false) {
     PassArgs a = base_args(ctx);
     if (from_scratch) {
         a.Qi = ctx->sc[0]; a.Pi = ctx->sc[1]; a.qsi = ctx->sc[2]; a.psi_i = ctx->sc[3]; a.wi = ctx->sc[4];
         flags |= PASS_WRITE_PSI;
+    }
+    const bool dep = (flags & PASS_DEPOSIT) != 0;
+    if (ctx->field_pending) flags |= PASS_FIELD_ACC;
+    bool deferred = false;
+    if (dep) {
+        a.acc = acc_buf(ctx, 1);
+        a.acc_m = acc_m_buf(ctx, 1);
+        a.acc_clr = acc_buf(ctx, 2);
+        a.acc_m_clr = acc_m_buf(ctx, 2);
+        if (defer && field_at_start(ctx)) {
+            flags &= ~(uint32_t)PASS_SOLVE;
+            deferred = true;
+        }
     }
     a.c1 = c1; a.c2 = c2; a.cd = cd;
     a.flags = flags & 0xffu;
@@ -265,6 +323,9 @@ swpic_status enqueue_pass(swpic_ctx *ctx, double c1, double c2, double cd, uint3
         CK(launch_pass(ctx->prec, ctx->dec, ctx->mode, a, grid, ctx->tpb, smem, ctx->stream));
         ctx->launches += 1;
     }
+    if (dep) ctx->acc_cur = (ctx->acc_cur + 1) % 3;
+    if (deferred) ctx->field_pending = true;
+    else if (flags & (PASS_SOLVE | PASS_FIELD_ACC)) ctx->field_pending = false;
     // Runs without particles have no CTA to finish them: their field stays zero,
     // and they get no step counts or diagnostic records.
     return SWPIC_OK;
@@ -317,8 +378,8 @@ swpic_status prepare(swpic_ctx *ctx, bool keep_steps) {
     }
     s = upload_runs(ctx);
     if (s != SWPIC_OK) return s;
-    CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_acc_m, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
+    s = clear_accumulators(ctx);
+    if (s != SWPIC_OK) return s;
     CK(cudaMemsetAsync(ctx->d_done, 0, sizeof(unsigned long long) * ctx->R, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_diag_acc, 0, sizeof(double) * 2 * ctx->R, ctx->stream));
     CK(cudaMemsetAsync(ctx->d_err, 0, sizeof(int32_t) * ctx->R, ctx->stream));
@@ -450,10 +511,10 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
     auto alloc = [&](void **p, size_t bytes) { return cudaMalloc(p, std::max<size_t>(bytes, 16)) == cudaSuccess; };
     bool ok = true;
     ok &= alloc((void **)&ctx->d_runs, sizeof(RunDev) * R);
-    ok &= alloc((void **)&ctx->d_acc, sizeof(unsigned long long) * mo);
+    ok &= alloc((void **)&ctx->d_acc, sizeof(unsigned long long) * 3 * (size_t)mo);
     ok &= alloc((void **)&ctx->d_snap, sizeof(long long) * mo);
     ok &= alloc((void **)&ctx->d_gauge, sizeof(long long) * R);
-    ok &= alloc((void **)&ctx->d_acc_m, sizeof(unsigned long long) * mo);
+    ok &= alloc((void **)&ctx->d_acc_m, sizeof(unsigned long long) * 3 * (size_t)mo);
     ok &= alloc((void **)&ctx->d_done, sizeof(unsigned long long) * R);
     ok &= alloc(&ctx->d_table, (size_t)mo * 2 * es);
     ok &= alloc((void **)&ctx->d_b, sizeof(double) * mo);
@@ -482,10 +543,10 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
                    cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(SWPIC_ECUDA);
     cudaMemset(ctx->d_err, 0, sizeof(int32_t) * R);
-    cudaMemset(ctx->d_acc, 0, sizeof(unsigned long long) * mo);
+    cudaMemset(ctx->d_acc, 0, sizeof(unsigned long long) * 3 * (size_t)mo);
     cudaMemset(ctx->d_snap, 0, sizeof(long long) * mo);
     cudaMemset(ctx->d_gauge, 0, sizeof(long long) * R);
-    cudaMemset(ctx->d_acc_m, 0, sizeof(unsigned long long) * mo);
+    cudaMemset(ctx->d_acc_m, 0, sizeof(unsigned long long) * 3 * (size_t)mo);
     cudaMemset(ctx->d_done, 0, sizeof(unsigned long long) * R);
     cudaMemset(ctx->d_steps, 0, sizeof(long long) * R);
     cudaMemset(ctx->d_ring_count, 0, sizeof(int32_t) * R);
@@ -545,7 +606,7 @@ swpic_status enqueue_desc(swpic_ctx *ctx, const PassDesc &p, int *timed) {
         if (s != SWPIC_OK) return s;
         CK(cudaEventRecord(ctx->events[2 * (*timed)], ctx->stream));
     }
-    swpic_status s = enqueue_pass(ctx, p.c1, p.c2, p.cd, p.flags, p.sort_before);
+    swpic_status s = enqueue_pass(ctx, p.c1, p.c2, p.cd, p.flags, p.sort_before, true);
     if (s != SWPIC_OK) return s;
     if (timed) {
         CK(cudaEventRecord(ctx->events[2 * (*timed) + 1], ctx->stream));
@@ -711,8 +772,8 @@ swpic_status swpic_refresh(swpic_ctx *ctx) { return prepare(ctx, false); }
 swpic_status swpic_deposit(swpic_ctx *ctx) {
     swpic_status s = ensure_prepared(ctx);
     if (s != SWPIC_OK) return s;
-    CK(cudaMemsetAsync(ctx->d_acc, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
-    CK(cudaMemsetAsync(ctx->d_acc_m, 0, sizeof(unsigned long long) * ctx->total_mesh, ctx->stream));
+    s = clear_accumulators(ctx);
+    if (s != SWPIC_OK) return s;
     s = enqueue_pass(ctx, 0.0, 0.0, 0.0, PASS_DEPOSIT | PASS_NO_WRITE, false);
     if (s != SWPIC_OK) return s;
     PassArgs b = base_args(ctx);
@@ -729,6 +790,7 @@ swpic_status swpic_solve_field(swpic_ctx *ctx) {
     b.flags = PASS_SOLVE;
     CK(launch_solve_runs(ctx->prec, b, 256, solve_smem_bytes(ctx->max_nx), ctx->stream));
     ctx->launches += 1;
+    ctx->field_pending = false;
     return SWPIC_OK;
 }
 
@@ -773,12 +835,14 @@ swpic_status swpic_step(swpic_ctx *ctx, int32_t n_steps, int32_t diag_every) {
         // chunks of G full passes; their pattern (diagnostics, sorts) repeats with `period`
         const int64_t a = d > 0 ? d : 1, b = can_sort(ctx) ? ctx->resort : 1;
         const int64_t period = a / gcd64(a, b) * b;
-        const int64_t G = period >= 64 ? period : period * ((64 + period - 1) / period);
+        int64_t G = period >= 64 ? period : period * ((64 + period - 1) / period);
+        if (G % 3) G *= 3;      // a replay leaves the accumulator rotation where it found it
         while (t + G <= s0 + n && G <= 4096) {
-            char key[160];
-            std::snprintf(key, sizeof(key), "G%lld/p%lld/d%d/r%d/t%d/b%d/s%d", (long long)G,
+            char key[200];
+            std::snprintf(key, sizeof(key), "G%lld/p%lld/d%d/r%d/t%d/b%d/s%d/a%d/f%d/m%d", (long long)G,
                           (long long)(t % period), d, can_sort(ctx) ? ctx->resort : 0, ctx->tpb,
-                          ctx->bpsm, pass_stages(ctx));
+                          ctx->bpsm, pass_stages(ctx), ctx->acc_cur, ctx->field_pending ? 1 : 0,
+                          field_at_start(ctx) ? 1 : 0);
             auto it = ctx->graph_cache.find(key);
             if (it == ctx->graph_cache.end()) {
                 if (ctx->graph_cache.size() >= 32) clear_graphs(ctx);
@@ -792,6 +856,8 @@ swpic_status swpic_step(swpic_ctx *ctx, int32_t n_steps, int32_t diag_every) {
                 cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
                 ge.kernels = ctx->launches - l0;
                 ge.n_passes = (int)G;
+                ge.acc_cur_after = ctx->acc_cur;
+                ge.field_pending_after = ctx->field_pending;
                 ctx->launches = l0;
                 if (q != SWPIC_OK) { if (g) cudaGraphDestroy(g); return q; }
                 if (e != cudaSuccess) return fail_cuda(ctx, "cudaStreamEndCapture", e);
@@ -802,6 +868,8 @@ swpic_status swpic_step(swpic_ctx *ctx, int32_t n_steps, int32_t diag_every) {
             }
             CK(cudaGraphLaunch(it->second.exec, ctx->stream));
             ctx->launches += it->second.kernels;
+            ctx->acc_cur = it->second.acc_cur_after;
+            ctx->field_pending = it->second.field_pending_after;
             t += G;
         }
     }
@@ -1083,6 +1151,22 @@ swpic_status swpic_get_pipeline(const swpic_ctx *ctx, int32_t *requested, int32_
     if (!ctx) return SWPIC_EINVAL;
     if (requested) *requested = ctx->pipe;
     if (effective) *effective = pass_stages(ctx);
+    return SWPIC_OK;
+}
+
+swpic_status swpic_set_field_solve(swpic_ctx *ctx, int32_t mode) {
+    if (!ctx) return SWPIC_EINVAL;
+    if (mode != SWPIC_FIELD_SOLVE_AUTO && mode != SWPIC_FIELD_SOLVE_LAST_CTA && mode != SWPIC_FIELD_SOLVE_AT_START)
+        return fail(ctx, SWPIC_EINVAL, "field solve mode must be 0 (auto), 1 (last CTA) or 2 (at start)");
+    ctx->field_solve = mode;
+    clear_graphs(ctx);
+    return SWPIC_OK;
+}
+
+swpic_status swpic_get_field_solve(const swpic_ctx *ctx, int32_t *mode, int32_t *effective) {
+    if (!ctx) return SWPIC_EINVAL;
+    if (mode) *mode = ctx->field_solve;
+    if (effective) *effective = field_at_start(ctx) ? SWPIC_FIELD_SOLVE_AT_START : SWPIC_FIELD_SOLVE_LAST_CTA;
     return SWPIC_OK;
 }
 

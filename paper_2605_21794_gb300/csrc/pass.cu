@@ -1,5 +1,6 @@
 // The particle pass of the decorated-particle step (sm_103a), and the per-run
-// field solve that the last CTA of each run performs at the end of a pass.
+// field solve, done either by the last CTA of each run at the end of the
+// depositing pass or by every CTA of the next pass at its start.
 //
 // Floating-point contraction is off for this file (-fmad=false): every fused
 // multiply-add is written as fma(), so each copy of the particle arithmetic
@@ -27,11 +28,17 @@
 // does not depend on thread scheduling.  At the end of its particle range a
 // CTA adds its mesh into the run's global int64 accumulator.
 //
-// The CTA that completes the last particles of a run (a completion counter,
-// no spinning) then removes the mean of b (Eq. neutrality / zero-mean test
+// The field solve removes the mean of b (Eq. neutrality / zero-mean test
 // space), solves A Phi = btilde (Eq. lin-sys) by Gauss's law
 //   e_j - e_{j-1} = btilde_j,  sum_j e_j = 0       (e_i = -phi_h' on element i)
-// and rebuilds the (phi_h', phi_h'') table for the next pass.
+// and builds the (phi_h', phi_h'') table.  Either the CTA that completes the
+// last particles of a run (a completion counter, no spinning) does it at the
+// end of the depositing pass and writes the table to global memory, or
+// (PASS_FIELD_ACC) every CTA of the next pass does it at its start into its
+// own shared-memory table while its first particle copies are in flight, so
+// that no pass ends in a one-CTA solve; the accumulators rotate over three
+// buffers so that the deposit being solved, the one being filled and the one
+// being cleared are never the same.
 #include <math.h>
 
 #include "f32x2.cuh"
@@ -281,30 +288,36 @@ __device__ __forceinline__ float ll_to_float(long long x) {
     return __uint_as_float(bits | (x < 0 ? 0x80000000u : 0u));
 }
 
-// One CTA.  full = false: snapshot only (swpic_deposit's read-out).
+// One CTA, all its threads.  src (src_m: P2 midpoint loads) is the run's
+// slice of a finished deposit; s_p is nx int64 of shared scratch.  The table
+// goes to tab_sh (shared, when given) and, with globals, to the run's global
+// table together with the snapshot, W, E_amp and the gauge; without globals
+// nothing outside the CTA is written.  full = false: snapshot only
+// (swpic_deposit's read-out).  The deposit itself is left as it is (the
+// accumulators rotate between passes).
 template <typename T, bool P2>
-__device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned char *smem, bool full) {
+__device__ void solve_run(const PassArgs &a, const RunDev &R, int r, long long *s_p,
+                          const unsigned long long *src, const unsigned long long *src_m,
+                          typename Vec2<T>::type *tab_sh, bool globals, bool full) {
     using T2 = typename Vec2<T>::type;
     __shared__ long long sh_ll[34];
     __shared__ __int128 sh_q[2][32];
     const int nx = R.nx, tid = threadIdx.x, nt = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
-    long long *s_p = reinterpret_cast<long long *>(smem);      // raw acc, then e_int
-    unsigned long long *acc = a.acc + R.mesh_off;
     long long *snap = a.snap + R.mesh_off;
     const int off = R.mesh_off;
     const int per = (nx + nt - 1) / nt;
     const int j0 = min(nx, tid * per), j1 = min(nx, j0 + per);
-    const long long c = a.gauge[r];           // reference for the field energy: the last gauge mean
+    // reference for the field energy: the last gauge mean
+    const long long c = globals ? a.gauge[r] : 0ll;
 
     // 1. load (coalesced; a thread's loads are independent and unrolled, so
-    //    the L2 round trips overlap), snapshot, clear
+    //    the L2 round trips overlap), snapshot
 #pragma unroll 8
     for (int j = tid; j < nx; j += nt) {
-        const long long v = (long long)__ldcg(acc + j);
+        const long long v = (long long)__ldcg(src + j);
         s_p[j] = v;
-        snap[j] = v;
-        if (full) acc[j] = 0ull;
+        if (globals) snap[j] = v;
     }
     if (!full) return;
     __syncthreads();
@@ -352,12 +365,14 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
         const long long e = P - (long long)(j + 1) * q;
         s_p[j] = e;
         es += (__int128)e;
-        const long long e8 = (e - c) >> 8;                      // squares of 2^55 sum safely in int128
-        e2 += (__int128)e8 * e8;
+        if (globals) {
+            const long long e8 = (e - c) >> 8;                  // squares of 2^55 sum safely in int128
+            e2 += (__int128)e8 * e8;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         es += shfl_xor_i128(es, o);
-        e2 += shfl_xor_i128(e2, o);
+        if (globals) e2 += shfl_xor_i128(e2, o);    // globals is uniform over the CTA
     }
     __syncthreads();                                            // sh_ll reads above are done
     if (lane == 0) { sh_q[0][warp] = es; sh_q[1][warp] = e2; }
@@ -393,7 +408,7 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
     //    nx (m - c)^2 (no cancellation while c is near m), W = (h/2) sum e^2
     //    2^-2k, E_amp, in FP64 for either state precision (the sums are exact
     //    integers; only their conversion and the products round).
-    if (tid == 0) {
+    if (globals && tid == 0) {
         __int128 e2sum = 0;
         for (int w = 0; w < nw; ++w) e2sum += sh_q[1][w];
         const double d8 = ((double)(mean_i - c) + (double)mrem * R.inv_nx) * (1.0 / 256.0);
@@ -406,8 +421,9 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
         if (!isfinite(W)) atomicOr(a.err + r, kErrNonFinite);
         a.gauge[r] = mean_i;
     }
-    // the table nodes go to the threads after warp 0 (all threads if there is one warp)
-    const int tb = (nt > 32) ? 32 : 0, nt2 = nt - tb;
+    // the table nodes go to the threads after warp 0 while thread 0 forms the
+    // energy (to all threads when there is one warp or no energy to form)
+    const int tb = (globals && nt > 32) ? 32 : 0, nt2 = nt - tb;
     const int per2 = (nx + nt2 - 1) / nt2;
     const int t2 = tid - tb;
     const int k0 = (t2 < 0) ? nx : min(nx, t2 * per2), k1 = (t2 < 0) ? nx : min(nx, k0 + per2);
@@ -429,8 +445,7 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
             T2 t;
             t.x = (T)(-(ll_to_float(ej_i - mean_i) * finv));
             if constexpr (p2) {
-                const long long bm = (long long)__ldcg(a.acc_m + off + j);
-                a.acc_m[off + j] = 0ull;
+                const long long bm = (long long)__ldcg(src_m + j);
                 const float beta = (0.25f * ll_to_float(3 * bm - 2 * q) - 0.5f * ll_to_float(rem) * R.inv_nxf) * finv;
                 t.y = (T)beta;
                 beta2 += (double)(beta * beta);
@@ -439,7 +454,8 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
             } else {
                 t.y = (T)(ll_to_float(em_i - ep_i) * finv * f_half_inv_h);
             }
-            tab[j] = t;
+            if (tab_sh) tab_sh[j] = t;
+            if (globals) tab[j] = t;
         }
     } else {
         const double mfrac = (double)mrem * R.inv_nx;
@@ -455,8 +471,7 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
             T2 t;
             t.x = (T)(-efield(ej_i, j));
             if constexpr (p2) {
-                const long long bm = (long long)__ldcg(a.acc_m + off + j);
-                a.acc_m[off + j] = 0ull;
+                const long long bm = (long long)__ldcg(src_m + j);
                 const double beta = (0.25 * (double)(3 * bm - 2 * q) - 0.5 * (double)rem * R.inv_nx) * inv;
                 t.y = (T)beta;
                 beta2 += beta * beta;
@@ -465,10 +480,11 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, unsigned ch
             } else {
                 t.y = (T)((efield(em_i, jm) - efield(ep_i, jp)) * (0.5 * R.inv_h));
             }
-            tab[j] = t;
+            if (tab_sh) tab_sh[j] = t;
+            if (globals) tab[j] = t;
         }
     }
-    if constexpr (p2) {
+    if (p2 && globals) {
         // P2 field energy: (1/2) int phi'^2 = (h/2) sum (e^2 + beta^2/3); E_amp = (2W/L)^(1/2)
         __shared__ double sh_b[32];
         const double b2 = block_sum_d(beta2, sh_b);
@@ -1046,12 +1062,17 @@ template <typename T, int MODE>
 __host__ __device__ __forceinline__ size_t mesh_bytes(int max_nx) {
     return (size_t)(max_nx + 1) * (MODE == SWPIC_DEPOSIT_ATOMIC ? sizeof(T) : sizeof(unsigned long long));
 }
-// node mesh plus, for P2, the per-element midpoint mesh
+// node mesh plus, for P2, the per-element midpoint mesh; at least 8 bytes per
+// node, since a pass that solves its field at its start uses the area as the
+// solve's int64 scratch before it clears the mesh
 template <typename T, int MODE, int D2>
 __host__ __device__ __forceinline__ size_t mesh_bytes_all(int max_nx) {
-    return mesh_bytes<T, MODE>(max_nx) +
-           (D2 == SWPIC_D2_P2 ? (size_t)max_nx * (MODE == SWPIC_DEPOSIT_ATOMIC ? sizeof(T) : sizeof(unsigned long long))
-                              : 0);
+    const size_t m = mesh_bytes<T, MODE>(max_nx) +
+                     (D2 == SWPIC_D2_P2 ? (size_t)max_nx * (MODE == SWPIC_DEPOSIT_ATOMIC ? sizeof(T)
+                                                                                   : sizeof(unsigned long long))
+                                        : 0);
+    const size_t scratch = (size_t)max_nx * sizeof(long long);
+    return m > scratch ? m : scratch;
 }
 
 // Shared-memory layout of the pass: table | mesh | (bulk stream) mbarriers | stages.
@@ -1247,7 +1268,9 @@ __device__ void finish_run(const PassArgs &a, const RunDev &R, int r, unsigned c
     const bool diag = (fl & PASS_DIAG) != 0;
     DiagPre pre;
     if (diag && threadIdx.x == 0) diag_preload(a, r, pre);
-    if (fl & PASS_SOLVE) solve_run<T, P2>(a, R, r, smem, true);
+    if (fl & PASS_SOLVE)
+        solve_run<T, P2>(a, R, r, reinterpret_cast<long long *>(smem), a.acc + R.mesh_off, a.acc_m + R.mesh_off,
+                         nullptr, true, true);
     if (threadIdx.x == 0) {
         if (diag) diag_write(a, R, r, pre);
         if (fl & PASS_COUNT_STEP) a.steps[r] += 1;
@@ -1285,8 +1308,8 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
     __syncthreads();
 
     // Programmatic dependent launch: this grid may be scheduled while the
-    // previous pass's last CTA is still solving; wait for that grid to finish
-    // (and its writes to be visible) before touching any memory.
+    // previous pass is still finishing; wait for that grid to complete (and
+    // its writes to be visible) before touching any memory.
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const int64_t c0 = (int64_t)blockIdx.x * a.chunk;
     const int64_t c1 = min(c0 + a.chunk, a.n_total);
@@ -1312,8 +1335,25 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
         const int64_t s = pos, e = min(c1, R.p1);
         if (s >= e) { ++r; continue; }
         const int nx = R.nx;
-        const T2 *gtab = reinterpret_cast<const T2 *>(a.table) + R.mesh_off;
-        for (int j = threadIdx.x; j < nx; j += blockDim.x) s_tab[j] = gtab[j];
+        const bool owner = s == R.p0;             // this CTA holds the run's first particle
+        if (DEP && owner && a.acc_clr) {
+            // the accumulator that the next depositing pass fills (no pass reads it now)
+            for (int j = threadIdx.x; j < nx; j += blockDim.x) a.acc_clr[R.mesh_off + j] = 0ull;
+            if (D2 == SWPIC_D2_P2)
+                for (int j = threadIdx.x; j < nx; j += blockDim.x) a.acc_m_clr[R.mesh_off + j] = 0ull;
+        }
+        if (a.flags & PASS_FIELD_ACC) {
+            // the field of the deposit the previous pass left, solved by every
+            // CTA into its own table (the mesh area is the solve's scratch), so
+            // that no pass ends in a one-CTA solve; the first bulk copies of the
+            // segment are already in flight
+            solve_run<T, D2 == SWPIC_D2_P2>(a, R, r, reinterpret_cast<long long *>(s_mesh), a.acc_src + R.mesh_off,
+                                            a.acc_m_src + R.mesh_off, s_tab, owner, true);
+            __syncthreads();
+        } else {
+            const T2 *gtab = reinterpret_cast<const T2 *>(a.table) + R.mesh_off;
+            for (int j = threadIdx.x; j < nx; j += blockDim.x) s_tab[j] = gtab[j];
+        }
         if (DEP) {
             if (MODE == SWPIC_DEPOSIT_ATOMIC) {
                 T *m = reinterpret_cast<T *>(s_mesh);
@@ -1429,8 +1469,12 @@ __global__ void __launch_bounds__(1024) k_solve_runs(PassArgs a, int full) {
     if (r >= a.n_runs) return;
     const RunDev R = a.runs[r];
     if (full == 2) readout_run(a, R, smem);
-    else if (a.d2_mode == SWPIC_D2_P2) solve_run<T, true>(a, R, r, smem, full != 0);
-    else solve_run<T, false>(a, R, r, smem, full != 0);
+    else if (a.d2_mode == SWPIC_D2_P2)
+        solve_run<T, true>(a, R, r, reinterpret_cast<long long *>(smem), a.acc + R.mesh_off,
+                           a.acc_m + R.mesh_off, nullptr, true, full != 0);
+    else
+        solve_run<T, false>(a, R, r, reinterpret_cast<long long *>(smem), a.acc + R.mesh_off,
+                            a.acc_m + R.mesh_off, nullptr, true, full != 0);
 }
 
 // Phi from e: Phi_{j+1} = Phi_j - h e_j, then zero mean (one CTA per run)
@@ -1473,7 +1517,8 @@ size_t pass_smem_bytes(int prec, int max_nx, int mode, bool decorated, int tpb, 
     const size_t t2 = (prec == SWPIC_F64) ? 16 : 8;
     const size_t me = (mode == SWPIC_DEPOSIT_ATOMIC) ? ((prec == SWPIC_F64) ? 8 : 4) : 8;
     const size_t tb = (size_t)max_nx * t2,
-                 mb = (size_t)(max_nx + 1) * me + (d2_mode == SWPIC_D2_P2 ? (size_t)max_nx * me : 0);
+                 mb0 = (size_t)(max_nx + 1) * me + (d2_mode == SWPIC_D2_P2 ? (size_t)max_nx * me : 0),
+                 mb = mb0 > (size_t)max_nx * 8 ? mb0 : (size_t)max_nx * 8;     // as mesh_bytes_all
     size_t push = tb + mb;
     if (stages >= 2)
         push = stage_area_offset(tb, mb, tpb / 32, stages) +

@@ -71,6 +71,9 @@ enum PassFlags : uint32_t {
     PASS_WRITE_PSI = 8u,   // write psi* to the output arrays (input came from the sort buffer)
     PASS_COUNT_STEP = 16u, // last CTA advances the run's step counter
     PASS_READOUT = 32u,    // (solve kernel only) FP64 b, btilde, E from the snapshot
+    PASS_FIELD_ACC = 64u,  // every CTA solves the field of acc_src at its start (no table load);
+                           // the CTA holding a run's first particle also writes the run's
+                           // table, snapshot, W, E_amp and gauge to global memory
 };
 
 struct PassArgs {
@@ -85,7 +88,12 @@ struct PassArgs {
     const RunDev *runs;
     double c1, c2, cd;        // closing kick, opening kick, drift: fractions of dt
     uint32_t flags;
-    unsigned long long *acc;  // int64 bit patterns
+    unsigned long long *acc;  // int64 bit patterns: deposit target (and the source of the
+                              // last-CTA solve and of the solve kernel)
+    const unsigned long long *acc_src;    // PASS_FIELD_ACC: the deposit of the current positions
+    unsigned long long *acc_clr;          // depositing pass: zeroed by each run's first CTA
+    const unsigned long long *acc_m_src;  // P2: midpoint loads beside acc_src
+    unsigned long long *acc_m_clr;        // P2: beside acc_clr
     long long *snap;          // int64 snapshot of acc taken by the last solve (read-out)
     long long *gauge;         // [R] integer gauge mean of the last solve (reference of the next)
     unsigned long long *acc_m;  // P2: int64 bit patterns of the element-midpoint load (per element)

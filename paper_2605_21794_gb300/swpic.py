@@ -24,6 +24,7 @@ SWPIC_DEPOSIT_ATOMIC, SWPIC_DEPOSIT_DETERMINISTIC = 0, 1
 SWPIC_D2_LUMPED, SWPIC_D2_NODAL, SWPIC_D2_P2 = 0, 2, 3
 SWPIC_NX_MAX = 4096
 SWPIC_STATIC_NX_MAX = 4096
+SWPIC_FIELD_SOLVE_AUTO, SWPIC_FIELD_SOLVE_LAST_CTA, SWPIC_FIELD_SOLVE_AT_START = 0, 1, 2
 
 
 class swpic_config(C.Structure):
@@ -113,6 +114,8 @@ SIGNATURES = {
     "swpic_set_pipeline": (C.c_int, [_CTX, C.c_int32]),
     "swpic_get_pipeline": (C.c_int, [_CTX, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "swpic_set_wait_test": (C.c_int, [_CTX, C.c_int32, C.c_int64]),
+    "swpic_set_field_solve": (C.c_int, [_CTX, C.c_int32]),
+    "swpic_get_field_solve": (C.c_int, [_CTX, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]),
     "swpic_set_timing": (C.c_int, [_CTX, C.c_int32]),
     "swpic_pass_times": (C.c_int, [_CTX, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_int32)]),
     "swpic_launch_count": (C.c_int, [_CTX, C.POINTER(C.c_int64)]),
@@ -358,6 +361,17 @@ def swpic_get_pipeline(ctx):
     """(requested, effective) bulk-copy stage counts; 0 = register loads."""
     a, b = C.c_int32(), C.c_int32()
     _check(load_library().swpic_get_pipeline(ctx, C.byref(a), C.byref(b)), ctx)
+    return a.value, b.value
+
+
+def swpic_set_field_solve(ctx, mode):
+    _check(load_library().swpic_set_field_solve(ctx, int(mode)), ctx)
+
+
+def swpic_get_field_solve(ctx):
+    """(requested, effective) field-solve placement (SWPIC_FIELD_SOLVE_*)."""
+    a, b = C.c_int32(), C.c_int32()
+    _check(load_library().swpic_get_field_solve(ctx, C.byref(a), C.byref(b)), ctx)
     return a.value, b.value
 
 

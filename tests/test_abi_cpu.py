@@ -64,6 +64,7 @@ int main(void) {
   printf("%zu %zu %zu\\n", offsetof(swpic_config, diag_capacity), offsetof(swpic_diag, step),
          offsetof(swpic_lattice, decorate));
   printf("%d %d %d\\n", SWPIC_ABI_VERSION, SWPIC_NX_MAX, SWPIC_STATIC_NX_MAX);
+  printf("%d %d %d\\n", SWPIC_FIELD_SOLVE_AUTO, SWPIC_FIELD_SOLVE_LAST_CTA, SWPIC_FIELD_SOLVE_AT_START);
   return 0;
 }''')
     exe = tmp_path / "layout"
@@ -77,6 +78,8 @@ int main(void) {
     assert offs == [swpic.swpic_config.diag_capacity.offset, swpic.swpic_diag.step.offset,
                     swpic.swpic_lattice.decorate.offset]
     assert [int(x) for x in lines[2].split()] == [1, swpic.SWPIC_NX_MAX, swpic.SWPIC_STATIC_NX_MAX]
+    assert [int(x) for x in lines[3].split()] == [swpic.SWPIC_FIELD_SOLVE_AUTO, swpic.SWPIC_FIELD_SOLVE_LAST_CTA,
+                                                  swpic.SWPIC_FIELD_SOLVE_AT_START]
 
 
 def test_status_strings_and_version_without_gpu(lib):
@@ -104,6 +107,7 @@ def test_create_rejects_bad_configs_before_touching_the_device(lib):
 def test_null_context_is_rejected(lib):
     from paper_2605_21794_gb300 import swpic
     assert lib.swpic_step(None, 1, 0) == swpic.SWPIC_EINVAL
+    assert lib.swpic_set_field_solve(None, 0) == swpic.SWPIC_EINVAL
     assert lib.swpic_deposit(None) == swpic.SWPIC_EINVAL
     lib.swpic_destroy(None)
 

@@ -1,7 +1,8 @@
 """The machinery around the step, through the C ABI: the bounded device
 wait (failure detection without a GPU fault), the autotuner, CUDA-graph
-replay against direct launches, the 1D fixed-point overflow report, and a
-checkpoint loaded into a context that has already stepped."""
+replay against direct launches, the 1D fixed-point overflow report, a
+checkpoint loaded into a context that has already stepped, and the two
+placements of the field solve."""
 import json
 import os
 
@@ -201,3 +202,59 @@ def test_load_into_a_context_that_has_stepped(tmp_path):
     assert dgot.shape[0] <= 4
     np.testing.assert_array_equal(dgot[-3:, 0], dref[-3:, 0])
     np.testing.assert_allclose(dgot[-3:, 6], dref[-3:, 6], rtol=1e-13)
+
+
+@pytest.mark.parametrize("precision,d2_mode,runs", [(32, 0, 1), (64, 0, 1), (32, 3, 3), (64, 2, 3), (32, 0, 6)])
+def test_field_solved_at_pass_start_equals_last_cta_solve(precision, d2_mode, runs):
+    """The two placements of the field solve (swpic_set_field_solve): each
+    depositing pass ending in a one-CTA solve, or every CTA of the next pass
+    solving the finished deposit at its start.  Deterministic deposit, a call
+    of 60 steps (direct launches) and one of 200 (a graph of 195 passes),
+    several runs and phi'' readings, weak decorations (a noisy random plasma
+    with the default ones grows them past the fixed-point headroom within a
+    few hundred steps): states, mesh charges and fields are equal bit for
+    bit, records up to the order of the FP64 atomics that combine CTA
+    partials."""
+    need_gpu()
+    from paper_2605_21794_gb300 import swpic
+    sizes = [70001, 33333, 50002, 20000, 41111, 9999][:runs]
+    cfg = [(L * (1 + 0.25 * r), DT, NX, n) for r, n in enumerate(sizes)]
+    parts = [W.random_state(n, Lr, seed=40 + r, nx=NX, dipole_scale=0.02) for r, (Lr, _, _, n) in enumerate(cfg)]
+    st = {k: np.concatenate([p[k] for p in parts]) for k in parts[0]}
+    out = []
+    for mode in (swpic.SWPIC_FIELD_SOLVE_LAST_CTA, swpic.SWPIC_FIELD_SOLVE_AT_START):
+        sim = swpic.Simulation(cfg, precision=precision, deposit_mode=1, d2_mode=d2_mode, resort_every=7,
+                               diag_capacity=512)
+        try:
+            swpic.swpic_set_field_solve(sim.ctx, mode)
+            assert swpic.swpic_get_field_solve(sim.ctx) == (mode, mode)
+            sim.init_particles(st)
+            sim.step(60, 3)
+            sim.step(200, 5)
+            out.append((sim.state(), [sim.mesh(r) for r in range(runs)],
+                        [sim.diagnostics(r) for r in range(runs)]))
+        finally:
+            sim.close()
+    (a, ma, da), (b, mb, db) = out
+    assert _states_equal(a, b)
+    for r in range(runs):
+        for k in ("b", "E"):
+            assert np.array_equal(ma[r][k], mb[r][k]), (r, k)
+    for r in range(runs):
+        assert da[r].shape == db[r].shape
+        scale = np.abs(db[r]).max(axis=0) + 1e-300
+        assert (np.abs(da[r] - db[r]) <= 1e-12 * scale).all(), r
+
+
+def test_field_solve_placement_default_follows_the_run_count():
+    need_gpu()
+    from paper_2605_21794_gb300 import swpic
+    for runs, eff in ((1, swpic.SWPIC_FIELD_SOLVE_AT_START), (4, swpic.SWPIC_FIELD_SOLVE_AT_START),
+                      (5, swpic.SWPIC_FIELD_SOLVE_LAST_CTA)):
+        sim = swpic.Simulation([(L, DT, NX, 1000)] * runs, precision=32)
+        try:
+            assert swpic.swpic_get_field_solve(sim.ctx) == (swpic.SWPIC_FIELD_SOLVE_AUTO, eff)
+            with pytest.raises(swpic.SwpicError):
+                swpic.swpic_set_field_solve(sim.ctx, 3)
+        finally:
+            sim.close()
