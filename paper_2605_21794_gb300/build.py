@@ -14,12 +14,13 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libswpic.so")
-SOURCES = ["api.cu", "pass.cu", "sort.cu", "init.cu", "kmeans.cu", "static_deposit.cu", "api2d.cu", "pass2d.cu"]
+SOURCES = ["api.cu", "pass.cu", "pass64.cu", "sort.cu", "init.cu", "kmeans.cu", "static_deposit.cu", "api2d.cu",
+           "pass2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 # the particle pass writes its fused multiply-adds out, and the k-means
 # assignment takes FP32 decisions from separately rounded operations
-PER_SOURCE = {"pass.cu": ["-fmad=false"], "kmeans.cu": ["-fmad=false"]}
+PER_SOURCE = {"pass.cu": ["-fmad=false"], "pass64.cu": ["-fmad=false"], "kmeans.cu": ["-fmad=false"]}
 
 
 def _nvcc():
@@ -40,7 +41,7 @@ def build(force=False, verbose=False):
     nvcc = _nvcc()
     headers = [os.path.join(INCLUDE, "swpic.h"), os.path.join(CSRC, "swpic_internal.cuh"),
                os.path.join(INCLUDE, "swpic2d.h"), os.path.join(CSRC, "swpic2d_internal.cuh"),
-               os.path.join(CSRC, "f32x2.cuh")]
+               os.path.join(CSRC, "f32x2.cuh"), os.path.join(CSRC, "pass_kernels.cuh")]
     objs, jobs = [], []
     for src in SOURCES:
         s = os.path.join(CSRC, src)

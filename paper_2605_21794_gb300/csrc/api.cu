@@ -234,6 +234,7 @@ PassArgs base_args(swpic_ctx *ctx) {
     a.d2_mode = ctx->d2;
     a.max_nx = ctx->max_nx;
     a.runs = ctx->d_runs;
+    if (ctx->R > 0) a.run0 = ctx->h_runs[0];
     a.acc = acc_buf(ctx, 0);
     a.acc_src = acc_buf(ctx, 0);
     a.snap = ctx->d_snap;
@@ -373,6 +374,8 @@ swpic_status prepare(swpic_ctx *ctx, bool keep_steps) {
         int k = kFixedBits;
         if (m > 0.0) k = kFixedBits - (int)std::ceil(std::log2(m));
         k = std::max(-1000, std::min(1000, k));
+        // captured graphs hold run 0 by value (PassArgs::run0): a new unit retires them
+        if (ctx->h_runs[r].fx_scale != std::ldexp(1.0, k)) clear_graphs(ctx);
         ctx->h_runs[r].fx_scale = std::ldexp(1.0, k);
         ctx->h_runs[r].fx_inv = std::ldexp(1.0, -k);
     }
@@ -396,9 +399,10 @@ swpic_status prepare(swpic_ctx *ctx, bool keep_steps) {
     if (s != SWPIC_OK) return s;
     ctx->last_diag_step = ctx->step;
     ctx->prepared = true;
-    // the captured step graphs stay valid: they hold the bound pointers and the
-    // launch shape (both clear them when they change), and read the unit, the
-    // step counters and the field from device memory
+    // the captured step graphs stay valid: they hold the bound pointers, the
+    // launch shape and run 0's parameters (all clear them when they change),
+    // and read the other runs' units, the step counters and the field from
+    // device memory
     return SWPIC_OK;
 }
 

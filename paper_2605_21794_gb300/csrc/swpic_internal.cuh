@@ -86,6 +86,8 @@ struct PassArgs {
     int32_t max_nx;           // largest nx of the batch (shared-memory layout)
     int32_t stages;           // >= 2: bulk-copy pipeline with this many stages; else register loads
     const RunDev *runs;
+    RunDev run0;              // runs[0] by value: a one-run pass reads its run from the
+                              // kernel parameters instead of global memory
     double c1, c2, cd;        // closing kick, opening kick, drift: fractions of dt
     uint32_t flags;
     unsigned long long *acc;  // int64 bit patterns: deposit target (and the source of the
@@ -122,6 +124,9 @@ size_t solve_smem_bytes(int max_nx);
 cudaError_t launch_pass(int prec, bool decorated, int mode, const PassArgs &a, int grid, int tpb,
                         size_t smem, cudaStream_t s);
 cudaError_t launch_solve_runs(int prec, const PassArgs &a, int tpb, size_t smem, cudaStream_t s);
+// FP64 particle passes (pass64.cu)
+cudaError_t launch_pass_f64(bool decorated, int mode, const PassArgs &a, int grid, int tpb, size_t smem,
+                            cudaStream_t s);
 cudaError_t launch_phi(const RunDev *runs, int n_runs, const double *efield, double *phi,
                        int max_nx, cudaStream_t s);
 
