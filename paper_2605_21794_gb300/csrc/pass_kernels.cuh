@@ -566,15 +566,24 @@ __device__ __forceinline__ void mesh_add(int key, T a0, T a1, void *mesh, T scal
     }
 }
 
+// P2: one particle's midpoint load into the CTA's per-element mesh
+template <typename T, int MODE>
+__device__ __forceinline__ void mesh_m_add(int key, T v, void *mesh_m, T scale, int32_t *err) {
+    if (MODE == SWPIC_DEPOSIT_ATOMIC) atomicAdd(reinterpret_cast<T *>(mesh_m) + key, v);
+    else atomicAdd(reinterpret_cast<unsigned long long *>(mesh_m) + key, to_fixed(v, scale, err));
+}
+
 // Warp-aggregated deposit: lanes holding the same element in consecutive lanes
 // form a segment; a segmented suffix sum (up to 5 shuffle steps, fixed order)
 // gives the segment's first lane the segment total, and only that lane touches
 // the shared mesh.  When no lane shares its element with the lane before (a
 // disordered plasma) the shuffles are skipped and every lane adds its own
-// value.  key < 0 marks an empty slot.  All 32 lanes must call this.
-template <typename T, int MODE>
+// value.  key < 0 marks an empty slot.  All 32 lanes must call this.  P2:
+// the element's midpoint load am is combined alongside and added to the
+// per-element mesh by the same lane.
+template <typename T, int MODE, bool P2 = false>
 __device__ __forceinline__ void warp_deposit(int key, T a0, T a1, void *mesh, T scale,
-                                             int32_t *err) {
+                                             int32_t *err, T am = T(0), void *mesh_m = nullptr) {
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int prev = __shfl_up_sync(full, key, 1);
@@ -590,10 +599,19 @@ __device__ __forceinline__ void warp_deposit(int key, T a0, T a1, void *mesh, T 
         for (int off = 1; off <= span; off <<= 1) {
             const T b0 = __shfl_down_sync(full, a0, off);
             const T b1 = __shfl_down_sync(full, a1, off);
-            if (lane + off <= seg_end) { a0 += b0; a1 += b1; }
+            T bm = T(0);
+            if (P2) bm = __shfl_down_sync(full, am, off);
+            if (lane + off <= seg_end) {
+                a0 += b0;
+                a1 += b1;
+                if (P2) am += bm;
+            }
         }
     }
-    if (head && key >= 0) mesh_add<T, MODE>(key, a0, a1, mesh, scale, err);
+    if (head && key >= 0) {
+        mesh_add<T, MODE>(key, a0, a1, mesh, scale, err);
+        if (P2) mesh_m_add<T, MODE>(key, am, mesh_m, scale, err);
+    }
 }
 
 // Push one particle; returns its deposit (element of the drifted Q, weights of
@@ -842,53 +860,52 @@ __device__ __forceinline__ void push_vector(typename Vec16<T>::type &q, typename
     if (DIAG) { th.mom.add(vm); th.kin.add(vk); }
 }
 
-// P2: one particle's midpoint load into the CTA's per-element mesh
-template <typename T, int MODE>
-__device__ __forceinline__ void mesh_m_add(int key, T v, void *mesh_m, T scale, int32_t *err) {
-    if (MODE == SWPIC_DEPOSIT_ATOMIC) atomicAdd(reinterpret_cast<T *>(mesh_m) + key, v);
-    else atomicAdd(reinterpret_cast<unsigned long long *>(mesh_m) + key, to_fixed(v, scale, err));
-}
 
 // Deposit one vector per lane.  Runs of equal elements inside the vector are
 // summed in registers first (fixed order); the first run of every lane joins
 // one warp-aggregated deposit (so a sorted or cold plasma, where whole
-// vectors share an element, costs one shared atomic per segment of lanes),
-// later runs go to the mesh directly.  All lanes of the warp must call this.
+// vectors share an element, costs one shared atomic per segment of lanes and
+// node, and with P2 one more for the element midpoint), later runs go to the
+// mesh directly.  All lanes of the warp must call this.
 template <typename T, int MODE, bool P2>
 __device__ __forceinline__ void deposit_vector(const VecOut<T> &o, void *s_mesh, void *s_mesh_m, T scale,
                                                int32_t *err) {
     constexpr int VW = Vec16<T>::n;
-    if (P2) {
-#pragma unroll
-        for (int l = 0; l < VW; ++l)
-            if (o.key[l] >= 0) mesh_m_add<T, MODE>(o.key[l], o.wm[l], s_mesh_m, scale, err);
-    }
     const int k0 = o.key[0];
-    T s0 = o.w0[0], s1 = o.w1[0];
+    T s0 = o.w0[0], s1 = o.w1[0], sm = P2 ? o.wm[0] : T(0);
     bool first = true;
     int kr = -1;
-    T r0 = T(0), r1 = T(0);
+    T r0 = T(0), r1 = T(0), rm = T(0);
 #pragma unroll
     for (int l = 1; l < VW; ++l) {
         const int k = o.key[l];
         if (first && k == k0) {
             s0 += o.w0[l];
             s1 += o.w1[l];
+            if (P2) sm += o.wm[l];
         } else {
             first = false;
             if (k == kr) {
                 r0 += o.w0[l];
                 r1 += o.w1[l];
+                if (P2) rm += o.wm[l];
             } else {
-                if (kr >= 0) mesh_add<T, MODE>(kr, r0, r1, s_mesh, scale, err);
+                if (kr >= 0) {
+                    mesh_add<T, MODE>(kr, r0, r1, s_mesh, scale, err);
+                    if (P2) mesh_m_add<T, MODE>(kr, rm, s_mesh_m, scale, err);
+                }
                 kr = k;
                 r0 = o.w0[l];
                 r1 = o.w1[l];
+                if (P2) rm = o.wm[l];
             }
         }
     }
-    if (kr >= 0) mesh_add<T, MODE>(kr, r0, r1, s_mesh, scale, err);
-    warp_deposit<T, MODE>(k0, s0, s1, s_mesh, scale, err);
+    if (kr >= 0) {
+        mesh_add<T, MODE>(kr, r0, r1, s_mesh, scale, err);
+        if (P2) mesh_m_add<T, MODE>(kr, rm, s_mesh_m, scale, err);
+    }
+    warp_deposit<T, MODE, P2>(k0, s0, s1, s_mesh, scale, err, sm, s_mesh_m);
 }
 
 // One warp turn (both particle streams) covers 512 bytes of every array:
