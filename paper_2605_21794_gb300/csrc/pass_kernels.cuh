@@ -1403,6 +1403,14 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
         }
         // every CTA has been scheduled by now: let the next pass launch early
         asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+        if (DIAG) {
+            // warp partials of the diagnostic sums first: their FP64 shuffle
+            // chain overlaps the flush below
+            const double m = warp_sum_d((double)th.mom.s + (double)(-th.mom.c));
+            const double k = warp_sum_d((double)th.kin.s + (double)(-th.kin.c));
+            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+            if (lane == 0) { s_red[w] = m; s_red[32 + w] = k; }
+        }
         __syncthreads();
         if (DEP) {
             unsigned long long *gacc = a.acc + R.mesh_off;
@@ -1430,11 +1438,6 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
             }
         }
         if (DIAG) {
-            const double m = warp_sum_d((double)th.mom.s + (double)(-th.mom.c));
-            const double k = warp_sum_d((double)th.kin.s + (double)(-th.kin.c));
-            const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-            if (lane == 0) { s_red[w] = m; s_red[32 + w] = k; }
-            __syncthreads();
             if (threadIdx.x == 0) {
                 double sm = 0.0, sk = 0.0;
                 for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { sm += s_red[q]; sk += s_red[32 + q]; }
@@ -1443,9 +1446,11 @@ __device__ __forceinline__ void pass_body(const PassArgs &a) {
             }
         }
         if (last_work) {
-            __threadfence();
+            // every thread's flush happens before the barrier; thread 0's fence
+            // then orders all of them before its count (release, cumulative)
             __syncthreads();
             if (threadIdx.x == 0) {
+                __threadfence();
                 const unsigned long long cnt = (unsigned long long)(e - s);
                 const unsigned long long prev = atomicAdd(a.run_done + r, cnt);
                 s_last = (prev + cnt == (unsigned long long)(R.p1 - R.p0)) ? 1 : 0;
