@@ -378,6 +378,7 @@ swpic_status prepare(swpic_ctx *ctx, bool keep_steps) {
         if (ctx->h_runs[r].fx_scale != std::ldexp(1.0, k)) clear_graphs(ctx);
         ctx->h_runs[r].fx_scale = std::ldexp(1.0, k);
         ctx->h_runs[r].fx_inv = std::ldexp(1.0, -k);
+        ctx->h_runs[r].fx_invf = (float)ctx->h_runs[r].fx_inv;
     }
     s = upload_runs(ctx);
     if (s != SWPIC_OK) return s;
@@ -482,6 +483,7 @@ swpic_status create_impl(const swpic_config *cfgs, int R, const int64_t *offsets
         d.dtf = (float)c.dt;
         d.fx_scale = std::ldexp(1.0, 56);
         d.fx_inv = std::ldexp(1.0, -56);
+        d.fx_invf = (float)d.fx_inv;
         d.mesh_off = mo;
         ctx->nx[r] = c.nx;
         ctx->mesh_off[r] = mo;

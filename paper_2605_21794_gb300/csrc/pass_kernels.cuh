@@ -438,8 +438,10 @@ __device__ void solve_run(const PassArgs &a, const RunDev &R, int r, long long *
     if (sizeof(T) == 4) {
         // FP32 table straight from the exact integers; the sub-quantum
         // gauge/remainder terms (< nx quanta) are below FP32 resolution
-        const float finv = opaque((float)inv);                  // power of two: exact
-        const float f_inv_h = opaque((float)R.inv_h), f_half_inv_h = opaque((float)(0.5 * R.inv_h));
+        // the FP32 units from the run parameters (rounded once on the host:
+        // no FP64 conversions on this GPU's narrow FP64 pipe here)
+        const float finv = R.fx_invf;                           // power of two: exact
+        const float f_inv_h = R.inv_hf, f_half_inv_h = 0.5f * R.inv_hf;   // 0.5 scales exactly
         for (int j = k0; j < k1; ++j) {
             const int jm = (j == 0) ? nx - 1 : j - 1, jp = (j == nx - 1) ? 0 : j + 1;
             const long long ej_i = s_p[j], em_i = s_p[jm], ep_i = s_p[jp];

@@ -61,6 +61,7 @@ struct RunDev {
     float inv_hf_lo;         // (nx/L) - inv_hf, so Q nx/L = Q inv_hf + Q inv_hf_lo to ~2^-48
     float L_lo;              // L - Lf: the FP32 domain is [0, Lf + L_lo) in exact terms
     float hf, inv_nxf;       // FP32 h and 1/nx (diagnostics of FP32 runs)
+    float fx_invf;           // (float) fx_inv, set with fx_scale (the FP32 table's unit)
     int32_t nx, mesh_off;
 };
 
