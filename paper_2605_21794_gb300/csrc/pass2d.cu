@@ -8,7 +8,9 @@
 //                 dipole charge into a per-CTA shared mesh, flush to a global
 //                 64-bit fixed-point accumulator (Eq. swpic_poisson, S_h = delta);
 //                 in FP32 contexts its last CTA writes the diagnostic record and
-//                 solves the new field in FP32 (solve_tail_f32)
+//                 solves the new field in FP32 (solve_tail_f32); consecutive
+//                 passes use programmatic dependent launch (each waits for its
+//                 predecessor before it reads memory)
 //   FP64 contexts solve in four kernels:
 //   k_rows_fwd    node loads -> FP64, forward DFT of every mesh row
 //   k_cols        per column: forward DFT, divide by the Q1 stiffness symbol
@@ -304,6 +306,9 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
     T4 *tab = reinterpret_cast<T4 *>(smem);
     T *mesh = reinterpret_cast<T *>(smem + (size_t)rs * ny * sizeof(T4));
     const T4 *gtab = reinterpret_cast<const T4 *>(a.table);
+    // Programmatic dependent launch: this grid may be scheduled while the
+    // previous pass is still finishing; wait for it before touching memory.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (int k = threadIdx.x; k < nn; k += blockDim.x) {
         const int pk = (k >> lgx) * rs + (k & (nx - 1));
         tab[pk] = gtab[k];
@@ -422,6 +427,8 @@ __global__ void __launch_bounds__(256, 3) k_pass2d(PassArgs2d a) {
             atomicAdd(mesh + dj1 * rs + di1, d3);
         }
     }
+    // every CTA has been scheduled by now: let the next pass launch early
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     __syncthreads();
     if (DEP) {
         for (int k = threadIdx.x; k < nn; k += blockDim.x) {
@@ -700,7 +707,19 @@ cudaError_t launch_pass(int prec, bool decorated, bool deposit, bool diag, const
     if (e != cudaSuccess) return e;
     PassArgs2d copy = a;
     void *args[] = {&copy};
-    return cudaLaunchKernel(fn, dim3(grid), dim3(tpb), args, smem, s);
+    // programmatic dependent launch: the next pass's CTAs become resident while
+    // this one finishes (they wait for it in the kernel)
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(tpb);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
 }
 
 cudaError_t launch_bound(int prec, const PassArgs2d &a, double *out, int grid, cudaStream_t s) {
