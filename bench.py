@@ -199,29 +199,41 @@ def host_cores():
 
 
 def time_oracle(spec, cols, steps, warmup, diag_every, d2_mode=0, threads=1):
-    """Seconds for `steps` oracle steps on a `cols`-column sample, per step
-    taken as [t(steps + 1) - t(1)] / steps: each oracle run factorises its
-    dense Poisson matrix once at set-up, and the difference leaves that
-    one-time cost out.  Returns (particles, seconds for `steps` steps,
-    threads used)."""
+    """Seconds for `steps` oracle steps on a `cols`-column sample.  Each oracle
+    run factorises its dense Poisson matrix once at set-up; a step is timed as
+    [t(M + 1 steps) - t(1 step)] / M, which leaves that one-time cost out.
+    For the P1 fields M = max(steps, 50) and each time is the best of two
+    runs, so that the steps outweigh the run-to-run spread of the
+    factorisation; the P2 field solves a dense system every step (seconds a
+    step, far above that spread): M = steps, one run each.  Returns
+    (particles, seconds for `steps` steps, threads used, M)."""
     import oracle as O
     used = O.set_threads(threads)
+    m, reps = (steps, 1) if d2_mode == 3 else (max(steps, 50), 2)
     try:
         lat = oracle_sample_spec(spec, cols)
         st = O.init_lattice(lat)
         if warmup > 0:
             st = O.run(st, spec.nx, lat.L, spec.dt, warmup, diag_every=diag_every, d2_mode=d2_mode,
                        decorated=spec.decorated)
-        t0 = time.perf_counter()
-        O.run(st, spec.nx, lat.L, spec.dt, 1, diag_every=diag_every, d2_mode=d2_mode,
-              decorated=spec.decorated)
-        t1 = time.perf_counter()
-        O.run(st, spec.nx, lat.L, spec.dt, steps + 1, diag_every=diag_every, d2_mode=d2_mode,
-              decorated=spec.decorated)
-        t2 = time.perf_counter()
+
+        def run_s(k):
+            best = 1e30
+            for _ in range(reps):
+                t0 = time.perf_counter()
+                O.run(st, spec.nx, lat.L, spec.dt, k, diag_every=diag_every, d2_mode=d2_mode,
+                      decorated=spec.decorated)
+                best = min(best, time.perf_counter() - t0)
+            return best
+
+        t_one = run_s(1)
+        t_many = run_s(m + 1)
     finally:
         O.set_threads(1)
-    return lat.n, max((t2 - t1) - (t1 - t0), 1e-9), used
+    per_step = (t_many - t_one) / m
+    if per_step <= 0.0:                     # spread larger than the steps: bound from above
+        per_step = t_many / (m + 1)
+    return lat.n, per_step * steps, used, m
 
 
 def run_reference(args, spec):
@@ -233,12 +245,13 @@ def run_reference(args, spec):
     # the oracle's P2 field is a dense (2 nx + 1)^2 solve every step: a few steps only
     steps = min(args.steps, 5) if d2 == 3 else args.steps
     warm = min(args.warmup, 1) if d2 == 3 else args.warmup
-    n, dt, cores = time_oracle(spec, cols, steps, warm, args.diag_every, d2, threads=host_cores())
+    n, dt, cores, m = time_oracle(spec, cols, steps, warm, args.diag_every, d2, threads=host_cores())
     value = n * steps / dt
-    sample = ("%d of %d lattice columns (%d particles) of %s, %d steps after %d warm-up steps, "
-              "plain-C FP64 oracle, particle loops on %d host threads; seconds per step = "
-              "[t(K+1 steps) - t(1 step)]/K (the one-time dense LU of each oracle run left out)" %
-              (cols, spec.lattice.nq, n, spec.name, steps, warm, cores))
+    sample = ("%d of %d lattice columns (%d particles) of %s, after %d warm-up steps, plain-C FP64 "
+              "oracle, particle loops on %d host threads; seconds per step = [t(M+1 steps) - "
+              "t(1 step)]/M with M = %d%s (the one-time dense LU of each oracle run left out)" %
+              (cols, spec.lattice.nq, n, spec.name, warm, cores, m,
+               "" if d2 == 3 else ", each the best of two runs"))
     config = dict(workload_config(spec, args, None),
                   sample={"lattice_columns": cols, "particles": n, "steps": steps,
                           "note": "each step of the oracle arm is one oracle step of this sample of "
@@ -967,16 +980,16 @@ def cpu_baseline_leg(spec, args):
     into blocks, or_set_threads) and one, on the same bounded sample."""
     cols = 256                     # 256 x 4096 = 1,048,576 particles
     k = 20
-    n, dt, cores = time_oracle(spec, cols, k, 0, args.diag_every, threads=host_cores())
-    n1, dt1, _ = time_oracle(spec, cols, 5, 0, args.diag_every, threads=1)
+    n, dt, cores, m = time_oracle(spec, cols, k, 0, args.diag_every, threads=host_cores())
+    n1, dt1, _, m1 = time_oracle(spec, cols, 5, 0, args.diag_every, threads=1)
     how = ("%d of %d lattice columns (%d particles) of %s from the lattice start, plain-C FP64 "
-           "oracle; seconds per step = [t(K+1 steps) - t(1 step)]/K (the one-time dense LU of "
-           "each oracle run left out)" % (cols, spec.lattice.nq, n, spec.name))
+           "oracle; seconds per step = [t(M+1 steps) - t(1 step)]/M, each the best of two runs "
+           "(the one-time dense LU of each oracle run left out)" % (cols, spec.lattice.nq, n, spec.name))
     return {"value": n * k / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": how + ", K = %d, particle loops on %d host threads" % (k, cores),
+            "sample": how + ", M = %d, particle loops on %d host threads" % (m, cores),
             "host_cores": host_cores(),
             "single_core": {"value": n1 * 5 / dt1, "unit": UNIT, "cores": 1, "kind": "oracle",
-                            "sample": how + ", K = 5, serial loops"},
+                            "sample": how + ", M = %d, serial loops" % m1},
             "init_kmeans": kmeans_oracle_sample(), "p2_elements": p2_oracle_sample(spec, args),
             "two_d": two_d_oracle_sample(args)}
 
@@ -1000,7 +1013,7 @@ def p2_oracle_sample(spec, args):
     """The oracle with the P2 field (a dense (2 nx + 1)^2 LU solve every step)
     on 64 lattice columns, 3 steps, one core."""
     cols, k = 64, 3
-    n, dt, _ = time_oracle(spec, cols, k, 0, args.diag_every, 3)
+    n, dt, _, _ = time_oracle(spec, cols, k, 0, args.diag_every, 3)
     return {"value": n * k / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": "%d of %d lattice columns (%d particles), %d steps, P2 field" %
                       (cols, spec.lattice.nq, n, k)}
