@@ -2,7 +2,8 @@
 run, and the only collective is the MAX of the timed region over ranks.  This
 checks that host logic with two gloo ranks on the CPU (no GPU): the job time is
 the slowest rank's on every rank, the whole-job value counts every replica, and
-the reference arm prints only on rank 0."""
+the reference arm prints only on rank 0; the oracle step timer of the CPU
+baseline reads steps, not timing noise."""
 import io
 import os
 import socket
@@ -70,3 +71,18 @@ def test_reference_arm_prints_only_on_rank_zero(monkeypatch):
     with contextlib.redirect_stdout(buf):
         bench.run_reference(args, W.bump_on_tail())
     assert buf.getvalue() == ""
+
+
+def test_oracle_step_timer_reads_steps_not_noise():
+    """The CPU baseline's per-step time is [t(M+1 steps) - t(1 step)]/M with
+    M = max(K, 50) for the P1 fields: even at K = 2 the rate is a plausible
+    single-core figure, not the run-to-run spread of the one-time dense LU
+    divided by two steps."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    spec = W.bump_on_tail()
+    n, secs, used, m = bench.time_oracle(spec, 4, 2, 0, 1, threads=1)
+    assert (n, used, m) == (4 * spec.lattice.nv, 1, 50)
+    rate = n * 2 / secs
+    assert 0.0 < rate < 1e10, rate
