@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--stages", type=int, default=None, help="bulk-copy stages (0 = register loads; no autotune)")
     ap.add_argument("--only-2d", action="store_true",
                     help="run only the 2D2V leg (K timed steps) and print its JSON object")
+    ap.add_argument("--only-sort", action="store_true",
+                    help="run only the sort leg (the main line's workload) and print its JSON object")
     ap.add_argument("--side-2d", type=int, default=4096,
                     help="2D leg: particles = side^2 = (lattice side)^4 (4096 = the 2D workload, 64^4)")
     ap.add_argument("--workload", choices=["bump_on_tail", "landau_strong", "landau_strong_pic"],
@@ -353,6 +355,12 @@ def main():
     tpb, bpsm, resort = swpic.swpic_get_launch(sim.ctx)
     stages = swpic.swpic_get_pipeline(sim.ctx)[1]
     restore(sim)
+    if args.only_sort:
+        if rank == 0:
+            print(json.dumps(sort_leg(torch, swpic, sim, n, args, (tpb, bpsm, resort), restore, arrays)),
+                  flush=True)
+        sim.close()
+        return
 
     def barrier():
         if world > 1:
@@ -439,6 +447,7 @@ def main():
         line["two_d"] = two_d_leg(torch, swpic, args)
         line["strong_landau"] = method_legs(torch, swpic, args, timed)
         line["fp32_diag_error"] = fp32_diag_error_leg(torch, swpic, spec, args)
+        line["sort"] = sort_leg(torch, swpic, sim, n, args, (tpb, bpsm, resort), restore, arrays)
         line["cpu_baseline"] = cpu_baseline_leg(spec, args)
     elif rank == 0:
         restore(sim)
@@ -497,6 +506,88 @@ def e2e_leg(torch, swpic, sim, n, args):
             "note": "swpic_step_host on the state after the W warm-up steps: H2D of the %d state "
                     "arrays, field set-up, K steps, D2H of %d arrays, all inside the timed region" %
                     (len(ins), len(outs))}
+
+
+def sort_leg(torch, swpic, sim, n, args, launch, restore, arrays):
+    """The stable sort by element (Sec. 5's deposit wants particles grouped by
+    element; histogram -> scan -> stable scatter into the sort buffer), timed
+    as the step runs it: a re-sort before every full pass, plain launches
+    with CUDA events around each pass on the context stream.  The device time
+    of the whole call (events on the same stream) minus the passes' own times
+    is the span of the sort kernels between them, per sort.  One sort moves
+    44 B per FP32 decorated particle: the histogram reads Q, the scatter reads
+    the five arrays and writes them to the sort buffer (the count and
+    position tables, chunks x nx entries, are left out).
+    - every_step: K sorts from the state of the timed steps, a re-sort
+      before every full pass (the first sort sees the lattice order, the
+      others the previous sort's order moved by one step);
+    - random_order: one sort of a randomly permuted copy of that state (the
+      first re-sort after a permutation; the passes before and after it are
+      not counted), median of three permutations."""
+    tpb, bpsm, resort = launch
+    es = 4 if sim.precision == 32 else 8
+    bytes_per_sort = (es * (5 if sim.decorated else 3) * 2 + es) * n
+    peak, peak_src = measured_peak()
+
+    def sort_span(k_steps):
+        swpic.swpic_set_launch(sim.ctx, tpb, bpsm, 1)
+        swpic.swpic_set_timing(sim.ctx, 1)
+        torch.cuda.synchronize()
+        l0 = swpic.swpic_launch_count(sim.ctx)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        # keep the stream busy (~2 ms) while the call is enqueued, so that no
+        # host-side launch latency lands between the events
+        with torch.cuda.stream(sim.stream):
+            torch.cuda._sleep(4_000_000)
+        e0.record(sim.stream)
+        sim.step(k_steps, args.diag_every)
+        e1.record(sim.stream)
+        e1.synchronize()
+        total = e0.elapsed_time(e1)
+        pass_ms = swpic.swpic_pass_times(sim.ctx)
+        launches = swpic.swpic_launch_count(sim.ctx) - l0
+        swpic.swpic_set_timing(sim.ctx, 0)
+        swpic.swpic_set_launch(sim.ctx, tpb, bpsm, resort)
+        sorts, rem = divmod(launches - len(pass_ms), 5)      # 5 launches per sort
+        if rem or sorts <= 0:
+            raise RuntimeError("sort leg: %d launches for %d passes" % (launches, len(pass_ms)))
+        return (total - float(np.sum(pass_ms))) / sorts, sorts
+
+    def entry(ms, sorts):
+        gbs = bytes_per_sort / (ms / 1e3) / 1e9
+        return {"ms_per_sort": ms, "sorts": sorts, "particles_per_s": n / (ms / 1e3),
+                "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                             "frac": gbs / peak, "traffic": None, "peak_source": peak_src,
+                             "algorithmic_bytes_per_launch": bytes_per_sort}}
+
+    restore(sim)
+    sim.step(args.warmup, args.diag_every)
+    k = max(3, min(args.steps, 20))
+    ms_in, sorts_in = sort_span(k)
+    rand = []
+    for rep in range(3):
+        restore(sim)
+        sim.step(args.warmup, args.diag_every)
+        g = torch.Generator(device=sim.Q.device)
+        g.manual_seed(20260 + rep)
+        perm = torch.randperm(n, device=sim.Q.device, generator=g)
+        torch.cuda.synchronize()
+        for t in arrays(sim):
+            t.copy_(t[perm])
+        torch.cuda.synchronize()
+        swpic.swpic_refresh(sim.ctx)
+        rand.append(sort_span(2))     # passes at steps 0, 1 and the closing one; one sort before step 1
+    restore(sim)
+    ms_r = float(np.median([r[0] for r in rand]))
+    return {"kernels": "k_sort_hist, k_scan_reduce, k_scan_top, k_scan_down, k_sort_scatter",
+            "bytes_per_particle": bytes_per_sort // n,
+            "every_step": entry(ms_in, sorts_in), "random_order": entry(ms_r, 1),
+            "note": "sort time = device time of the call minus its timed passes, per sort; "
+                    "every_step: K sorts from the state of the timed steps, a re-sort before every "
+                    "full pass (the first sees the lattice order, the others the previous sort's "
+                    "order moved by one step); random_order: one sort of a randomly permuted state; "
+                    "traffic null (the ncu summary covers the first sort on a smaller lattice)"}
 
 
 def kmeans_leg(torch, swpic):
